@@ -1,0 +1,177 @@
+/*
+ * sogrand.h -- C ABI of libsogrand: soft-output GRAND (SOGRAND) decoding of
+ * short even linear codes and block-turbo decoding of product codes on one
+ * NVIDIA GB300 (sm_103a).
+ *
+ * Method: P. Yuan, M. Medard, K. Galligan, K. R. Duffy, "Soft-output (SO)
+ * GRAND and iterative decoding to outperform LDPCs", arXiv 2310.10737.
+ *
+ * Conventions shared by every call
+ *   - LLR = log p(r | bit 0) / p(r | bit 1) (Sec. V-B); a negative LLR is a
+ *     hard 1, an LLR of exactly 0 is a hard 0.
+ *   - The SISO input of a word is lambda = fl32(L_Ch + L_A), one FP32
+ *     rounding; every decision (hard bits, reliability ranks, the 1-line
+ *     parameter) is taken on that value.
+ *   - Query order: 1-line ORBGRAND (the paper's choice, Sec. VI): patterns by
+ *     increasing cost = (sum of reliability ranks) + c * (Hamming weight),
+ *     ties by weight then lexicographic rank vector; ranks by |lambda|
+ *     ascending with ties to the lower bit index; c is the rounded
+ *     intercept/slope of the exact least-squares line through the sorted
+ *     |lambda| quantised to 1/256 (saturating at 4096), clamped to [0, n].
+ *   - Even codes (Sec. III-B): only noise patterns with the parity of the
+ *     hard decision are queried, and the soft output is conditioned on that
+ *     parity class: phi = (2^k - 1)/(2^(n-1) - 1) in the Corollary of Sec. IV.
+ *   - Device pointers are CUDA device (or managed) memory of the current
+ *     device; `stream` is a cudaStream_t (NULL = legacy default stream).
+ *     Calls are asynchronous on `stream` unless stated; results are valid
+ *     once the stream has reached the call.  The caller owns every buffer.
+ *   - Every call returns SOGRAND_OK or one of the error codes below and
+ *     writes nothing on an argument error.  sogrand_strerror() names them.
+ */
+#ifndef SOGRAND_H
+#define SOGRAND_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SOGRAND_OK 0
+#define SOGRAND_EINVAL 1       /* invalid argument (sizes, pointers, code) */
+#define SOGRAND_ENOMEM 2       /* device or host allocation failed */
+#define SOGRAND_ECUDA 3        /* a CUDA runtime call failed */
+#define SOGRAND_ETIMEOUT 4     /* a bounded device wait gave up */
+#define SOGRAND_EUNSUPPORTED 5 /* valid but not implemented (e.g. row code != column code) */
+
+/* Opaque code object: parity-check matrix, its device copy and the query-order
+ * tables.  Immutable after creation apart from table growth (see
+ * sogrand_code_reserve); may be shared by threads and streams. */
+typedef struct sogrand_code sogrand_code;
+
+/*
+ * Create a code from its (n-k) x n parity-check matrix H (Sec. III-B:
+ * x is a codeword iff H x = 0).
+ *   n      2 <= n <= 128
+ *   k      1 <= k < n, n - k <= 64
+ *   H      HOST pointer, (n-k) x n row-major, entries 0 or 1
+ *   even   1: the code is even (all-ones vector in the row space of H) and
+ *          the search is restricted to the parity class of the hard
+ *          decision (Sec. III-B); EINVAL if the code is not even.
+ *          0: all patterns are queried, phi = (2^k-1)/(2^n-1).
+ *   out    receives the object (NULL on error)
+ * Builds the query-order tables for query caps up to 10^4 and copies them to
+ * the current device (synchronous).  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int sogrand_code_create(int n, int k, const uint8_t *H, int even, sogrand_code **out);
+
+/* Release a code and its device memory.  No decode using it may be in
+ * flight.  NULL is ignored. */
+void sogrand_code_destroy(sogrand_code *code);
+
+/*
+ * Make the query-order tables cover query caps up to max_query_cap
+ * (synchronous; reallocates the tables, so no decode using `code` may be in
+ * flight).  Decodes with a larger cap call this themselves.
+ * Errors: EINVAL (max_query_cap < 1 or > 2^24), ENOMEM, ECUDA.
+ */
+int sogrand_code_reserve(sogrand_code *code, int64_t max_query_cap);
+
+/* Length n and dimension k of a code (either pointer may be NULL). */
+int sogrand_code_info(const sogrand_code *code, int *n, int *k);
+
+/*
+ * SOGRAND soft-input soft-output decoding of n_words independent words
+ * (Fig. siso; Sec. IV Corollary; Sec. V-B eq. LLRi).  One warp per word.
+ *   llr_ch     device [n_words][n] channel LLRs L_Ch
+ *   llr_a      device [n_words][n] a-priori LLRs L_A, or NULL for zeros
+ *   L          list size, 1 <= L <= 16: the search stops at the L-th codeword
+ *   query_cap  1 <= cap <= 2^24: the search also stops after this many queries
+ *   thr        0 disables; else the search also stops as soon as the predicted
+ *              probability that the list misses the transmitted codeword
+ *              (eq. app_approxlist) drops below thr (checked at each new word)
+ *   outputs (device, each may be NULL):
+ *   hard       [n_words][n] u8: 1 where L_APP < 0
+ *   llr_app    [n_words][n] L_APP (eq. LLRi)
+ *   llr_ext    [n_words][n] L_E = L_APP - lambda (0 when the list is empty)
+ *   p_miss     [n_words] probability that the codeword is not in the list
+ *   queries    [n_words] codebook queries made; -1 marks a word with a
+ *              non-finite input LLR (its outputs: L_APP = lambda, L_E = 0,
+ *              p_miss = 1, empty list)
+ *   list_words [n_words][L][ceil(n/64)] u64: the listed codewords in query
+ *              order, bit i of the word = bit (i mod 64) of u64 (i / 64);
+ *              unused slots are 0
+ *   list_app   [n_words][L] APP of each listed codeword (eq. app_approx_correct)
+ *   list_count [n_words] number of listed codewords
+ * With an empty list (cap reached before any codeword) L_APP = lambda.
+ * May grow the tables (synchronous) if query_cap exceeds the reserved cap.
+ * Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int sogrand_decode(sogrand_code *code, int64_t n_words, const float *llr_ch, const float *llr_a, int L,
+                   int64_t query_cap, float thr, uint8_t *hard, float *llr_app, float *llr_ext, float *p_miss,
+                   int64_t *queries, uint64_t *list_words, float *list_app, int32_t *list_count, void *stream);
+
+/*
+ * Block turbo decoding of n_frames product codes (Sec. VI, Fig. turboDec):
+ * L_A = 0; each half iteration decodes every row (odd halves) or column (even
+ * halves) of every running frame with SOGRAND (lambda = L_Ch + fl32(alpha L_E)
+ * of the previous half), takes the hard decision of L_APP and stops a frame
+ * as soon as every row and column is a codeword; at most 2 * max_iter halves.
+ *   row_code, col_code  the component codes (must be the same object;
+ *                       EUNSUPPORTED otherwise)
+ *   llr_ch     device [n_frames][n][n] channel LLRs, row-major (bit (i, j) is
+ *              row i, column j)
+ *   L, query_cap, thr   as for sogrand_decode (query_cap < 2^(n-1), so the
+ *              search never exhausts the parity class)
+ *   alpha      extrinsic scaling, > 0 (the paper uses 0.5)
+ *   max_iter   1 <= max_iter <= 1000 full (row + column) iterations
+ *   outputs (device):
+ *   bits       [n_frames][ceil(n*n/8)] u8: the final hard decision, bit p =
+ *              i*n + j at byte p/8, bit p%8 (required)
+ *   half_iters [n_frames] half iterations run (may be NULL)
+ *   status     [n_frames] 0 decoded (all rows and columns codewords), 1 max
+ *              iterations reached, 2 non-finite input (may be NULL)
+ *   queries    [n_frames] total codebook queries (may be NULL)
+ * Allocates its scratch (about 4 n^2 + 8 n ceil(n/64) + 16 bytes per frame)
+ * stream-ordered on `stream` and reads a device flag between halves to stop
+ * early, so the call returns when the decode has finished.
+ * Errors: EINVAL, EUNSUPPORTED, ENOMEM, ECUDA.
+ */
+int product_decode(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch,
+                   int L, int64_t query_cap, float thr, float alpha, int max_iter, uint8_t *bits,
+                   int32_t *half_iters, uint8_t *status, int64_t *queries, void *stream);
+
+/*
+ * product_decode with one more output:
+ *   par_queries [n_frames] "parallelized" queries: the sum over half
+ *               iterations of the largest per-word query count (Sec. VI)
+ * and a diagnostic counter xf_words (device int32, may be NULL) that is
+ * incremented once per component decoding whose remaining-mass sum needed the
+ * extended-range arithmetic.
+ */
+int product_decode_ex(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch,
+                      int L, int64_t query_cap, float thr, float alpha, int max_iter, uint8_t *bits,
+                      int32_t *half_iters, uint8_t *status, int64_t *queries, int64_t *par_queries,
+                      int32_t *xf_words, void *stream);
+
+/*
+ * Test hook: the device's canonical query order for one word.
+ *   llr          HOST [n] lambda values
+ *   max_q        number of queries to list, >= 1
+ *   patterns_out HOST [max_q][ceil(n/64)] u64 noise patterns in RANK space:
+ *                bit r-1 set = the bit of reliability rank r is flipped
+ *   n_out        HOST: number written (fewer than max_q if the class ends)
+ *   c_out        HOST: the 1-line parameter used (may be NULL)
+ * Synchronous.  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int sogrand_trace_patterns(sogrand_code *code, const float *llr, int64_t max_q, uint64_t *patterns_out,
+                           int64_t *n_out, int32_t *c_out);
+
+/* Static text for an error code. */
+const char *sogrand_strerror(int err);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SOGRAND_H */

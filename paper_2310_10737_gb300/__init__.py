@@ -1,0 +1,16 @@
+"""GB300-native SOGRAND (soft-output GRAND) and product-code turbo decoding.
+
+Public entry points (same names as the C ABI in include/sogrand.h):
+
+* :class:`Code` / :func:`sogrand_code_create` -- a component code from H;
+* :func:`sogrand_decode` -- SISO decoding of many independent words;
+* :func:`product_decode` -- block turbo decoding of product codes;
+* :func:`sogrand_trace_patterns` -- the device's canonical query order (test hook).
+
+All compute runs in hand-written CUDA kernels for sm_103a (libsogrand.so);
+PyTorch only provides device memory and streams.
+"""
+from ._lib import (  # noqa: F401
+    Code, LIB_PATH, SograndError, load, product_decode, sogrand_code_create, sogrand_decode,
+    sogrand_trace_patterns, strerror, unpack_bits, unpack_words,
+)

@@ -1,0 +1,199 @@
+"""ctypes binding of libsogrand (include/sogrand.h).  Argument marshalling only:
+every step of decoding runs in the library's CUDA kernels.  PyTorch supplies
+device memory and the current stream.
+
+The library must have been built (``python -m paper_2310_10737_gb300.build`` or
+``__graft_entry__.build()``); importing the decode functions without it raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libsogrand.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ETIMEOUT, EUNSUPPORTED = range(6)
+
+_lock = threading.Lock()
+_lib = None
+
+
+class SograndError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {strerror(code)} ({code})")
+
+
+def load() -> C.CDLL:
+    """Load libsogrand.so; raises if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with `python -m paper_2310_10737_gb300.build` "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, i64, i32, f32 = C.c_void_p, C.c_int64, C.c_int, C.c_float
+        L.sogrand_code_create.argtypes = [i32, i32, vp, i32, C.POINTER(vp)]
+        L.sogrand_code_destroy.argtypes = [vp]
+        L.sogrand_code_destroy.restype = None
+        L.sogrand_code_reserve.argtypes = [vp, i64]
+        L.sogrand_code_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sogrand_decode.argtypes = [vp, i64, vp, vp, i32, i64, f32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.product_decode.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp]
+        L.product_decode_ex.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.sogrand_strerror.argtypes = [i32]
+        L.sogrand_strerror.restype = C.c_char_p
+        for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
+                     "product_decode", "product_decode_ex", "sogrand_trace_patterns"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+        return L
+
+
+def strerror(code: int) -> str:
+    try:
+        return load().sogrand_strerror(code).decode()
+    except RuntimeError:
+        return f"error {code}"
+
+
+def _check(rc: int, where: str):
+    if rc != OK:
+        raise SograndError(rc, where)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Code:
+    """A component code on the current device (sogrand_code_create)."""
+
+    def __init__(self, H, even: bool = True):
+        H = np.ascontiguousarray(H, dtype=np.uint8)
+        m, n = H.shape
+        self.n, self.k, self.m = n, n - m, m
+        self._H = H
+        h = C.c_void_p()
+        _check(load().sogrand_code_create(n, n - m, H.ctypes.data_as(C.c_void_p), int(bool(even)), C.byref(h)),
+               "sogrand_code_create")
+        self._h = h
+
+    @classmethod
+    def from_linear_code(cls, code, even=None):
+        return cls(code.H, code.even if even is None else even)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def reserve(self, max_query_cap: int):
+        _check(load().sogrand_code_reserve(self._h, int(max_query_cap)), "sogrand_code_reserve")
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().sogrand_code_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def sogrand_code_create(H, even: bool = True) -> Code:
+    return Code(H, even)
+
+
+def sogrand_decode(code: Code, llr_ch, llr_a=None, L: int = 4, query_cap: int = 10**4, thr: float = 0.0,
+                   lists: bool = True, stream=None) -> dict:
+    """Decode the rows of ``llr_ch`` ([W, n] float32 CUDA tensor); returns CUDA tensors."""
+    import torch
+    W, n = llr_ch.shape
+    assert n == code.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
+    if llr_a is not None:
+        assert llr_a.shape == llr_ch.shape and llr_a.dtype == torch.float32 and llr_a.is_contiguous()
+    dev = llr_ch.device
+    nm = (n + 63) // 64
+    out = dict(hard=torch.empty((W, n), dtype=torch.uint8, device=dev),
+               llr_app=torch.empty((W, n), dtype=torch.float32, device=dev),
+               llr_ext=torch.empty((W, n), dtype=torch.float32, device=dev),
+               p_miss=torch.empty(W, dtype=torch.float32, device=dev),
+               queries=torch.empty(W, dtype=torch.int64, device=dev))
+    if lists:
+        out.update(list_words=torch.empty((W, L, nm), dtype=torch.int64, device=dev),
+                   list_app=torch.empty((W, L), dtype=torch.float32, device=dev),
+                   list_count=torch.empty(W, dtype=torch.int32, device=dev))
+    rc = load().sogrand_decode(code.handle, W, _ptr(llr_ch), _ptr(llr_a), int(L), int(query_cap), float(thr),
+                               _ptr(out["hard"]), _ptr(out["llr_app"]), _ptr(out["llr_ext"]), _ptr(out["p_miss"]),
+                               _ptr(out["queries"]), _ptr(out.get("list_words")), _ptr(out.get("list_app")),
+                               _ptr(out.get("list_count")), _stream(stream))
+    _check(rc, "sogrand_decode")
+    return out
+
+
+def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
+                   max_iter: int = 20, col_code: Code | None = None, stream=None, out=None) -> dict:
+    """Decode [F, n, n] frames (float32 CUDA tensor); returns CUDA tensors."""
+    import torch
+    F, n, n2 = llr_ch.shape
+    assert n == n2 == code.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
+    dev = llr_ch.device
+    if out is None:
+        out = dict(bits=torch.empty((F, (n * n + 7) // 8), dtype=torch.uint8, device=dev),
+                   half_iters=torch.empty(F, dtype=torch.int32, device=dev),
+                   status=torch.empty(F, dtype=torch.uint8, device=dev),
+                   queries=torch.empty(F, dtype=torch.int64, device=dev),
+                   par_queries=torch.empty(F, dtype=torch.int64, device=dev),
+                   xf_words=torch.zeros(1, dtype=torch.int32, device=dev))
+    cc = col_code if col_code is not None else code
+    rc = load().product_decode_ex(code.handle, cc.handle, F, _ptr(llr_ch), int(L), int(query_cap), float(thr),
+                                  float(alpha), int(max_iter), _ptr(out["bits"]), _ptr(out["half_iters"]),
+                                  _ptr(out["status"]), _ptr(out["queries"]), _ptr(out["par_queries"]),
+                                  _ptr(out["xf_words"]), _stream(stream))
+    _check(rc, "product_decode")
+    return out
+
+
+def unpack_bits(bits, n: int):
+    """[F, ceil(n*n/8)] u8 (LSB first) -> [F, n, n] u8 (numpy)."""
+    b = np.asarray(bits.cpu() if hasattr(bits, "cpu") else bits, dtype=np.uint8)
+    F = b.shape[0]
+    return np.unpackbits(b, axis=1, bitorder="little")[:, :n * n].reshape(F, n, n)
+
+
+def unpack_words(words, n: int):
+    """[..., ceil(n/64)] int64 bit masks -> [..., n] u8 (numpy)."""
+    w = np.asarray(words.cpu() if hasattr(words, "cpu") else words).view(np.uint64)
+    bytes_ = w.astype("<u8").view(np.uint8).reshape(*w.shape[:-1], -1)
+    return np.unpackbits(bytes_, axis=-1, bitorder="little")[..., :n]
+
+
+def sogrand_trace_patterns(code: Code, llr, max_q: int):
+    """Device query order of one word: (rank masks [q, n] u8, c)."""
+    llr = np.ascontiguousarray(llr, dtype=np.float32)
+    nm = (code.n + 63) // 64
+    out = np.zeros((max_q, nm), dtype=np.uint64)
+    cnt = C.c_int64(0)
+    c = C.c_int32(0)
+    _check(load().sogrand_trace_patterns(code.handle, llr.ctypes.data_as(C.c_void_p), int(max_q),
+                                         out.ctypes.data_as(C.c_void_p), C.byref(cnt), C.byref(c)),
+           "sogrand_trace_patterns")
+    q = cnt.value
+    return unpack_words(out[:q].view(np.int64), code.n), int(c.value)

@@ -1,0 +1,66 @@
+// launch.h -- host-side launchers of the device kernels (library internal).
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "sg_common.h"
+
+namespace sg {
+
+// Component-word SISO decoding (sogrand_decode).  Pointers are device
+// memory; every output may be null.
+struct DecodeArgs {
+  int64_t n_words;
+  const float *llr_ch;   // [W][n]
+  const float *llr_a;    // [W][n] or null
+  uint8_t *hard;         // [W][n]
+  float *llr_app;        // [W][n]
+  float *llr_ext;        // [W][n]
+  float *p_miss;         // [W]
+  int64_t *queries;      // [W]
+  uint64_t *list_words;  // [W][L][nm]
+  float *list_app;       // [W][L]
+  int32_t *list_count;   // [W]
+  int32_t *xf_count;     // [1] words that needed the extended-range remainder (diagnostic)
+};
+
+// Block-turbo decoding of product codes (plain form: one launch per half).
+struct ProductArgs {
+  int64_t n_frames;
+  const float *llr_ch;   // [F][n][n] row-major
+  float alpha;
+  int32_t max_half;      // 2 * max iterations
+  float *le;             // [F][n][n] extrinsic state (scratch)
+  uint64_t *hb;          // [F][n][nm] hard decisions of the last half, rows or columns (scratch)
+  int32_t *fstate;       // [F] 0 running, 1 decoded, 2 max iterations, 3 invalid input (scratch)
+  int32_t *hmax;         // [F] max queries of the current half (scratch)
+  uint8_t *bits;         // [F][n*n/8] out, row-major, LSB first
+  int32_t *half_iters;   // [F] out
+  uint8_t *status;       // [F] out: 0 decoded, 1 max iterations, 2 invalid input
+  int64_t *queries;      // [F] out (total)
+  int64_t *par_queries;  // [F] out ("parallelized": sum over halves of the per-half max)
+  int32_t *active;       // [1] frames still running after the last check (scratch, may be null)
+  int32_t *xf_count;
+};
+
+template <int NPL, class SYN>
+cudaError_t launch_decode(const DevCode &code, const SisoParams &P, const DecodeArgs &a, cudaStream_t s);
+
+template <int NPL, class SYN>
+cudaError_t launch_trace(const DevCode &code, const float *lam, int max_q, uint64_t *out, int32_t *count,
+                         int32_t *c_out, cudaStream_t s);
+
+template <int NPL, class SYN>
+cudaError_t launch_product_init(const DevCode &code, const ProductArgs &a, cudaStream_t s);
+
+template <int NPL, class SYN>
+cudaError_t launch_product_half(const DevCode &code, const SisoParams &P, const ProductArgs &a, int half,
+                                cudaStream_t s);
+
+template <int NPL, class SYN>
+cudaError_t launch_product_check(const DevCode &code, const ProductArgs &a, int half, cudaStream_t s);
+
+int scratch_bytes(int npl, int syn_bytes, int jmax);
+
+}  // namespace sg

@@ -1,0 +1,144 @@
+"""GPU product-code turbo decoding (Sec. VI) against the oracle and against a
+host-driven composition of the GPU SISO.
+
+Free-running turbo decoding chains floating-point decisions: from the second
+half iteration on, the GPU's FP32 extrinsic values and the oracle's FP64 ones
+round differently, so a reliability near-tie may order two queries
+differently.  The bar is therefore:
+* frames the oracle finishes in the first half iteration (identical inputs
+  L_A = 0): bit-exact status, half iterations, queries and bits;
+* every frame: the decoded frame agrees with the oracle's in >= 99% of frames
+  and the block error rate lies inside the oracle's 95% Clopper-Pearson
+  interval;
+* against a composition of sogrand_decode half iterations driven from the host
+  with the same FP32 exchange arithmetic: bit-exact everything.
+"""
+import numpy as np
+import pytest
+
+from workloads import awgn_frames, ebch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(oracle_lib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_10737_gb300 as sg
+    return torch, sg
+
+
+def clopper_pearson(k, n, alpha=0.05):
+    from scipy.stats import beta
+    lo = 0.0 if k == 0 else beta.ppf(alpha / 2, k, n - k + 1)
+    hi = 1.0 if k == n else beta.ppf(1 - alpha / 2, k + 1, n - k)
+    return lo, hi
+
+
+def _decode(env, code, lch, **kw):
+    torch, sg = env
+    c = sg.Code.from_linear_code(code)
+    out = sg.product_decode(c, torch.from_numpy(np.ascontiguousarray(lch)).cuda(), **kw)
+    torch.cuda.synchronize()
+    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res["frames"] = sg.unpack_bits(out["bits"], code.n)
+    c.close()
+    return res
+
+
+@pytest.mark.parametrize("name,ebn0,boost,F,max_iter", [("ebch_32_26", 3.0, 1.5, 200, 4),
+                                                        ("ebch_16_11", 2.5, 1.5, 300, 20),
+                                                        ("ebch_64_57", 3.25, 3.0, 60, 20)])
+def test_product_matches_oracle(env, oracle_lib, name, ebn0, boost, F, max_iter):
+    code = ebch(name)
+    # every third frame at a higher Eb/N0, so that some finish in the first half
+    snr = np.where(np.arange(F) % 3 == 2, ebn0 + boost, ebn0)
+    U, X, lch = awgn_frames(code, F, snr, seed=300 + F)
+    g = _decode(env, code, lch, L=4, query_cap=10**4, alpha=0.5, max_iter=max_iter)
+    r = oracle_lib.product_batch(oracle_lib.OracleCode(code), lch, L=4, cap=10**4, alpha=0.5, max_iter=max_iter)
+    first = r["half_iters"] == 1
+    assert first.any()
+    np.testing.assert_array_equal(g["half_iters"][first], 1)
+    np.testing.assert_array_equal(g["status"][first], r["status"][first])
+    np.testing.assert_array_equal(g["queries"][first], r["queries"][first])
+    np.testing.assert_array_equal(g["frames"][first], r["bits"][first])
+    same = (g["frames"] == r["bits"]).reshape(F, -1).all(axis=1)
+    assert same.mean() >= 0.99, same.mean()
+    # success flag is consistent with an independent syndrome check
+    for f in range(F):
+        B = g["frames"][f]
+        valid = not code.syndrome(B).any() and not code.syndrome(B.T).any()
+        assert valid == (g["status"][f] == 0)
+    err_g = (g["frames"] != X).reshape(F, -1).any(axis=1).sum()
+    err_o = (r["bits"] != X).reshape(F, -1).any(axis=1).sum()
+    lo, hi = clopper_pearson(int(err_o), F)
+    assert lo <= err_g / F <= hi, (err_g, err_o)
+    assert (g["par_queries"] <= g["queries"]).all()
+
+
+def test_product_equals_host_composition_of_siso(env):
+    torch, sg = env
+    code = ebch("ebch_32_26")
+    n = code.n
+    F, max_iter, alpha = 64, 4, 0.5
+    U, X, lch = awgn_frames(code, F, 2.75, seed=400)
+    g = _decode(env, code, lch, L=4, query_cap=10**4, alpha=alpha, max_iter=max_iter)
+    c = sg.Code.from_linear_code(code)
+    Lch = torch.from_numpy(lch).cuda()
+    LE = torch.zeros_like(Lch)
+    done = np.zeros(F, bool)
+    halves = np.zeros(F, np.int32)
+    queries = np.zeros(F, np.int64)
+    B = np.zeros((F, n, n), np.uint8)
+    for h in range(1, 2 * max_iter + 1):
+        rows = h % 2 == 1
+        ch = Lch if rows else Lch.transpose(1, 2)
+        la = None if h == 1 else (torch.tensor(alpha, dtype=torch.float32, device="cuda") * LE)
+        if la is not None and not rows:
+            la = la.transpose(1, 2)
+        o = sg.sogrand_decode(c, ch.contiguous().reshape(F * n, n),
+                              None if la is None else la.contiguous().reshape(F * n, n), L=4, query_cap=10**4,
+                              lists=False)
+        le = o["llr_ext"].reshape(F, n, n)
+        hard = (o["llr_app"] < 0).reshape(F, n, n).cpu().numpy().astype(np.uint8)
+        q = o["queries"].reshape(F, n).sum(1).cpu().numpy()
+        if not rows:
+            le = le.transpose(1, 2)
+            hard = hard.transpose(0, 2, 1)
+        act = torch.from_numpy(~done).cuda()
+        LE = torch.where(act[:, None, None], le, LE)
+        for f in np.nonzero(~done)[0]:
+            queries[f] += q[f]
+            B[f] = hard[f]
+            halves[f] = h
+            if not code.syndrome(B[f]).any() and not code.syndrome(B[f].T).any():
+                done[f] = True
+        if done.all():
+            break
+    c.close()
+    np.testing.assert_array_equal(g["half_iters"], halves)
+    np.testing.assert_array_equal(g["queries"], queries)
+    np.testing.assert_array_equal(g["frames"], B)
+    np.testing.assert_array_equal(g["status"], np.where(done, 0, 1))
+
+
+def test_product_edge_cases(env, oracle_lib):
+    torch, sg = env
+    code = ebch("ebch_16_11")
+    U, X, lch = awgn_frames(code, 9, 3.0, seed=500)
+    lch[0] = (8.0 * (1.0 - 2.0 * X[0])).astype(np.float32)  # noiseless
+    lch[4, 3, 3] = np.nan
+    g = _decode(env, code, lch, L=4, query_cap=1000, alpha=0.5, max_iter=1)
+    assert g["half_iters"][0] == 1 and g["status"][0] == 0 and (g["frames"][0] == X[0]).all()
+    assert g["status"][4] == 2
+    assert (g["half_iters"] <= 2).all()
+    c = sg.Code.from_linear_code(code)
+    empty = torch.zeros((0, 16, 16), dtype=torch.float32, device="cuda")
+    sg.product_decode(c, empty)
+    with pytest.raises(sg.SograndError):
+        sg.product_decode(c, torch.from_numpy(lch).cuda(), query_cap=2 ** 15)  # whole parity class
+    c.close()
