@@ -1,0 +1,297 @@
+#!/usr/bin/env python3
+"""Decoded information bits/s of SOGRAND block-turbo decoding of the
+eBCH(64,57)^2 product code on GB300 (arXiv 2310.10737, Sec. VI workload).
+
+One step = one product_decode of the whole batch: 100,000 frames of
+eBCH(64,57)^2 (n = 4096, k = 3249), BPSK over AWGN with Eb/N0 swept
+2.5..4.0 dB in 0.25 dB steps (frame f at point f mod 7), FP32 channel LLRs,
+list size L = 4, query cap 10^4 per component decoding, alpha = 0.5, at most
+20 iterations with per-frame early stop.  Inputs (1.64 GB of LLRs) are larger
+than L2 and resident in HBM before timing.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+`--impl reference` times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (the method has no other implementation).
+Under torchrun (N > 1) every rank decodes its own batch (weak scaling, no
+collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+CODE = "ebch_64_57"
+FRAMES = 100_000
+EBN0 = [2.5 + 0.25 * i for i in range(7)]
+L_LIST, CAP, ALPHA, MAX_ITER, SEED = 4, 10**4, 0.5, 20, 2310
+SMS, INT32_LANES = 152, 128  # GB300: 152 SMs x 128 INT32/FP32 lanes per SM
+METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
+
+
+def log(msg):
+    """Progress on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.strftime('%H:%M:%S')}] {msg}", file=sys.stderr, flush=True)
+
+
+def workload_config(frames):
+    return {"workload": f"eBCH(64,57)^2 product code, {frames} frames, BPSK/AWGN Eb/N0 2.5:0.25:4.0 dB "
+                        "(frame f at point f mod 7), L=4, query cap 1e4, alpha 0.5, max 20 iterations, early stop",
+            "frames": frames, "n": 64, "k": 57, "info_bits_per_frame": 57 * 57, "L": L_LIST, "query_cap": CAP,
+            "max_iter": MAX_ITER, "alpha": ALPHA, "ebn0_db": EBN0, "seed": SEED,
+            "l2": "inputs larger than L2 (4 n^2 bytes per frame = 1.64 GB per 100k-frame step)"}
+
+
+def make_inputs(code, frames, seed, threads):
+    from workloads import awgn_frames
+    snr = np.array(EBN0)[np.arange(frames) % len(EBN0)]
+    return awgn_frames(code, frames, snr, seed=seed, threads=threads)
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({nm for r in rows for nm, v in zip(names, r[5:9]) if v.strip() == "Active"})
+        pw = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
+
+
+def cpu_oracle_rate(code, lch, threads):
+    """The oracle (FP64, plain C, all host cores) on a bounded sample: info bits/s."""
+    import oracle
+    oc = oracle.OracleCode(code)
+    t = time.perf_counter()
+    oracle.product_batch(oc, lch, L=L_LIST, cap=CAP, alpha=ALPHA, max_iter=MAX_ITER, threads=threads)
+    dt = time.perf_counter() - t
+    return lch.shape[0] * code.k * code.k / dt, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    from workloads import ebch
+    code = ebch(CODE)
+    cores = os.cpu_count() or 1
+    sample = args.ref_frames
+    _, _, lch = make_inputs(code, sample, SEED, cores)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(code, lch[: max(cores, 7)], cores)
+    times = []
+    for _ in range(args.steps):
+        _, dt = cpu_oracle_rate(code, lch, cores)
+        times.append(dt)
+    ms = 1000 * sum(times) / len(times)
+    value = sample * code.k * code.k / (ms / 1000)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "bits/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(FRAMES),
+            "cpu_baseline": {"value": value, "unit": "bits/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {sample} frames of the workload per step (all 7 Eb/N0 points)"},
+            "e2e": {"value": value, "unit": "bits/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--frames", type=int, default=FRAMES, help="frames per rank per step (default: the workload)")
+    ap.add_argument("--ref-frames", type=int, default=28, help="oracle sample per reference step")
+    ap.add_argument("--cpu-frames", type=int, default=112, help="oracle sample for cpu_baseline")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_10737_gb300 as sg
+    from workloads import ebch
+
+    code = ebch(CODE)
+    F = args.frames
+    cores = os.cpu_count() or 1
+    t0 = time.perf_counter()
+    U, X, lch = make_inputs(code, F, SEED + rank, cores)
+    log(f"inputs: {F} frames in {time.perf_counter() - t0:.1f} s")
+    host = torch.from_numpy(lch).pin_memory()
+    d_in = host.to(dev)
+    c = sg.Code.from_linear_code(code)
+    log("inputs resident on the device, code tables built")
+    n, k = code.n, code.k
+    out = dict(bits=torch.empty((F, n * n // 8), dtype=torch.uint8, device=dev),
+               half_iters=torch.empty(F, dtype=torch.int32, device=dev),
+               status=torch.empty(F, dtype=torch.uint8, device=dev),
+               queries=torch.empty(F, dtype=torch.int64, device=dev),
+               par_queries=torch.empty(F, dtype=torch.int64, device=dev),
+               weight_sum=torch.zeros(1, dtype=torch.int64, device=dev),
+               xf_words=torch.zeros(1, dtype=torch.int32, device=dev))
+
+    def step():
+        return sg.product_decode(c, d_in, L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER, out=out)
+
+    for i in range(args.warmup):
+        t0 = time.perf_counter()
+        step()
+        torch.cuda.synchronize()
+        log(f"warm-up step {i}: {1000 * (time.perf_counter() - t0):.1f} ms")
+    out["weight_sum"].zero_()
+    clocks = ClockSampler()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stream = torch.cuda.current_stream()
+    ev0.record(stream)
+    t_half = t_check = 0.0
+    launches = half_launches = 0
+    qtot = 0
+    for _ in range(args.steps):
+        o = step()
+        t_half += o["timing_ms"][0]
+        t_check += o["timing_ms"][1]
+        launches += o["launches"]
+        half_launches += o["launches"] // 2
+        qtot += int(out["queries"].sum().item())
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    log(f"timed: {args.steps} steps in {ms:.1f} ms")
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    wsum = int(out["weight_sum"].item())
+    info_bits = world * F * k * k * args.steps
+    value = info_bits / (ms / 1000)
+
+    # roofline of the dominant kernel (the half-iteration SISO kernel): integer ALU
+    ops = 2 * (qtot + wsum)  # per query: w syndrome XORs + 1 membership test, and w + 1 mass terms (Sec. IV)
+    sm_max = clk.get("sm_max_mhz") or 2070.0
+    peak = SMS * INT32_LANES * sm_max * 1e6 / 1e12  # Tops/s
+    achieved = ops / (t_half / 1000) / 1e12 if t_half > 0 else 0.0
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                "frac": achieved / peak if peak else None, "traffic": None,
+                "kernel": "k_product_half", "launches": half_launches,
+                "avg_launch_ms": t_half / max(half_launches, 1),
+                "ops_per_launch": ops / max(half_launches, 1),
+                "ops_def": "2 x (queries + summed pattern weights)",
+                "kernel_share": t_half / (t_half + t_check) if t_half + t_check else None,
+                "peak_def": "152 SMs x 128 INT32 lanes x max SM clock (derived)"}
+
+    # end to end through the C ABI on host buffers (copies inside the timed region)
+    bits_h = np.empty((F, n * n // 8), np.uint8)
+    hi_h = np.empty(F, np.int32)
+    st_h = np.empty(F, np.uint8)
+    q_h = np.empty(F, np.int64)
+    hout = dict(bits=bits_h, half_iters=hi_h, status=st_h, queries=q_h)
+    e2e_ms = []
+    for _ in range(max(args.e2e_steps, 1)):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        sg.product_decode_host(c, host, L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER, out=hout)
+        e2e_ms.append(1000 * (time.perf_counter() - t))
+    e2e_t = min(e2e_ms)
+    log(f"end to end: {e2e_ms}")
+    if dist:
+        t = torch.tensor([e2e_t], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_t = float(t.item())
+    e2e = {"value": world * F * k * k / (e2e_t / 1000), "unit": "bits/s",
+           "h2d_bytes_per_step": int(F * n * n * 4), "d2h_bytes_per_step": int(F * (n * n // 8 + 4 + 1 + 8)),
+           "api": "product_decode_host (C ABI, pinned host buffers)"}
+
+    # decoding quality of the timed configuration (BLER/BER/iterations/queries per Eb/N0)
+    frames = sg.unpack_bits(out["bits"], n)
+    ferr = (frames != X).reshape(F, -1)
+    info_err = (frames[:, :k, :k] != U).reshape(F, -1)
+    hi = out["half_iters"].cpu().numpy()
+    qf = out["queries"].cpu().numpy()
+    pq = out["par_queries"].cpu().numpy()
+    quality = {}
+    for i, e in enumerate(EBN0):
+        sel = np.arange(F) % len(EBN0) == i
+        quality[f"{e:.2f}"] = {"bler": float(ferr[sel].any(axis=1).mean()), "ber": float(info_err[sel].mean()),
+                               "iterations": float(hi[sel].mean() / 2), "queries_per_bit": float(qf[sel].mean() / (n * n)),
+                               "par_queries_per_bit": float(pq[sel].mean() / (n * n))}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_frames > 0:
+        rate, dt = cpu_oracle_rate(code, lch[: args.cpu_frames], cores)
+        log(f"cpu baseline: {args.cpu_frames} frames in {dt:.1f} s")
+        cpu = {"value": rate, "unit": "bits/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {args.cpu_frames} frames of the workload (16 per Eb/N0 point), {dt:.1f} s wall"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "bits/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(F),
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
+                "queries_per_s": world * qtot / (ms / 1000), "xf_words": int(out["xf_words"].item()),
+                "quality": quality, "form": "plain (one launch per half iteration)"}
+        print(json.dumps(line), flush=True)
+    c.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -141,18 +141,44 @@ int product_decode(sogrand_code *row_code, const sogrand_code *col_code, int64_t
                    int L, int64_t query_cap, float thr, float alpha, int max_iter, uint8_t *bits,
                    int32_t *half_iters, uint8_t *status, int64_t *queries, void *stream);
 
+/* Optional extra outputs and measurements of product_decode_ex.  Every
+ * member may be NULL. */
+typedef struct {
+  int64_t *par_queries;  /* device [n_frames]: "parallelized" queries, the sum
+                            over half iterations of the largest per-word query
+                            count (Sec. VI) */
+  uint64_t *weight_sum;  /* device [1]: incremented by the summed Hamming
+                            weights of every queried noise pattern */
+  int32_t *xf_words;     /* device [1]: incremented once per component decoding
+                            whose remaining-mass sum needed the extended-range
+                            arithmetic (all FP32-scaled terms underflowed) */
+  float *timing_ms;      /* HOST [2]: device time of the half-iteration kernels
+                            and of the frame-check kernels, from CUDA events on
+                            `stream` around each launch */
+  int32_t *launches;     /* HOST [1]: kernels launched by the call */
+} product_decode_stats;
+
 /*
- * product_decode with one more output:
- *   par_queries [n_frames] "parallelized" queries: the sum over half
- *               iterations of the largest per-word query count (Sec. VI)
- * and a diagnostic counter xf_words (device int32, may be NULL) that is
- * incremented once per component decoding whose remaining-mass sum needed the
- * extended-range arithmetic.
+ * product_decode with optional statistics (stats may be NULL; same errors).
  */
 int product_decode_ex(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch,
                       int L, int64_t query_cap, float thr, float alpha, int max_iter, uint8_t *bits,
-                      int32_t *half_iters, uint8_t *status, int64_t *queries, int64_t *par_queries,
-                      int32_t *xf_words, void *stream);
+                      int32_t *half_iters, uint8_t *status, int64_t *queries, product_decode_stats *stats,
+                      void *stream);
+
+/*
+ * product_decode on HOST buffers: copies llr_ch to the device, decodes and
+ * copies the results back before returning (device buffers are allocated
+ * stream-ordered on `stream` and freed before return).  Pinned host memory
+ * makes the copies asynchronous DMA; pageable memory works too.
+ *   llr_ch     HOST [n_frames][n][n]
+ *   bits       HOST [n_frames][ceil(n*n/8)] (required)
+ *   half_iters, status, queries  HOST [n_frames] (each may be NULL)
+ * Errors: as product_decode.
+ */
+int product_decode_host(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames,
+                        const float *llr_ch, int L, int64_t query_cap, float thr, float alpha, int max_iter,
+                        uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries, void *stream);
 
 /*
  * Test hook: the device's canonical query order for one word.

@@ -11,6 +11,7 @@ All compute runs in hand-written CUDA kernels for sm_103a (libsogrand.so);
 PyTorch only provides device memory and streams.
 """
 from ._lib import (  # noqa: F401
-    Code, LIB_PATH, SograndError, load, product_decode, sogrand_code_create, sogrand_decode,
+    Code, LIB_PATH, ProductStats, SograndError, load, product_decode, product_decode_host, sogrand_code_create,
+    sogrand_decode,
     sogrand_trace_patterns, strerror, unpack_bits, unpack_words,
 )

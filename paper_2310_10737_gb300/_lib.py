@@ -22,6 +22,12 @@ _lock = threading.Lock()
 _lib = None
 
 
+class ProductStats(C.Structure):
+    """product_decode_stats of include/sogrand.h."""
+    _fields_ = [("par_queries", C.c_void_p), ("weight_sum", C.c_void_p), ("xf_words", C.c_void_p),
+                ("timing_ms", C.POINTER(C.c_float)), ("launches", C.POINTER(C.c_int32))]
+
+
 class SograndError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = code
@@ -46,12 +52,14 @@ def load() -> C.CDLL:
         L.sogrand_code_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.sogrand_decode.argtypes = [vp, i64, vp, vp, i32, i64, f32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.product_decode.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp]
-        L.product_decode_ex.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp, vp, vp]
+        L.product_decode_ex.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp,
+                                        C.POINTER(ProductStats), vp]
+        L.product_decode_host.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp]
         L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
-                     "product_decode", "product_decode_ex", "sogrand_trace_patterns"):
+                     "product_decode", "product_decode_ex", "product_decode_host", "sogrand_trace_patterns"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -149,8 +157,9 @@ def sogrand_decode(code: Code, llr_ch, llr_a=None, L: int = 4, query_cap: int = 
 
 
 def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
-                   max_iter: int = 20, col_code: Code | None = None, stream=None, out=None) -> dict:
-    """Decode [F, n, n] frames (float32 CUDA tensor); returns CUDA tensors."""
+                   max_iter: int = 20, col_code: Code | None = None, stream=None, out=None, stats: bool = True) -> dict:
+    """Decode [F, n, n] frames (float32 CUDA tensor); returns CUDA tensors (and,
+    with stats, host-side timing_ms / launches)."""
     import torch
     F, n, n2 = llr_ch.shape
     assert n == n2 == code.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
@@ -161,13 +170,43 @@ def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: 
                    status=torch.empty(F, dtype=torch.uint8, device=dev),
                    queries=torch.empty(F, dtype=torch.int64, device=dev),
                    par_queries=torch.empty(F, dtype=torch.int64, device=dev),
+                   weight_sum=torch.zeros(1, dtype=torch.int64, device=dev),
                    xf_words=torch.zeros(1, dtype=torch.int32, device=dev))
     cc = col_code if col_code is not None else code
+    st = None
+    if stats:
+        tm = (C.c_float * 2)()
+        ln = (C.c_int32 * 1)()
+        st = ProductStats(_ptr(out.get("par_queries")), _ptr(out.get("weight_sum")), _ptr(out.get("xf_words")),
+                          C.cast(tm, C.POINTER(C.c_float)), C.cast(ln, C.POINTER(C.c_int32)))
     rc = load().product_decode_ex(code.handle, cc.handle, F, _ptr(llr_ch), int(L), int(query_cap), float(thr),
-                                  float(alpha), int(max_iter), _ptr(out["bits"]), _ptr(out["half_iters"]),
-                                  _ptr(out["status"]), _ptr(out["queries"]), _ptr(out["par_queries"]),
-                                  _ptr(out["xf_words"]), _stream(stream))
+                                  float(alpha), int(max_iter), _ptr(out["bits"]), _ptr(out.get("half_iters")),
+                                  _ptr(out.get("status")), _ptr(out.get("queries")),
+                                  C.byref(st) if st is not None else None, _stream(stream))
     _check(rc, "product_decode")
+    if stats:
+        out["timing_ms"] = (float(tm[0]), float(tm[1]))
+        out["launches"] = int(ln[0])
+    return out
+
+
+def product_decode_host(code: Code, llr_ch: np.ndarray, L: int = 4, query_cap: int = 10**4, thr: float = 0.0,
+                        alpha: float = 0.5, max_iter: int = 20, out=None, stream=None) -> dict:
+    """product_decode on HOST buffers (numpy or pinned CPU torch tensors); copies inside the call."""
+    F, n, _ = llr_ch.shape
+    if out is None:
+        out = dict(bits=np.empty((F, (n * n + 7) // 8), np.uint8), half_iters=np.empty(F, np.int32),
+                   status=np.empty(F, np.uint8), queries=np.empty(F, np.int64))
+
+    def hp(a):
+        if a is None:
+            return None
+        return C.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data_as(C.c_void_p)
+
+    rc = load().product_decode_host(code.handle, code.handle, F, hp(llr_ch), int(L), int(query_cap), float(thr),
+                                    float(alpha), int(max_iter), hp(out["bits"]), hp(out["half_iters"]),
+                                    hp(out["status"]), hp(out["queries"]), _stream(stream))
+    _check(rc, "product_decode_host")
     return out
 
 

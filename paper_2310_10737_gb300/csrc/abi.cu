@@ -21,9 +21,10 @@ struct sogrand_code {
   uint64_t *d_hcol = nullptr;  // [n]
   uint64_t *d_hrow = nullptr;  // [m][nm]
   void *d_tab = nullptr;
-  sg::DevTables tab{};
+  sg::DevOrder ord{};
   int jmax = 1;
   int64_t tab_cap = 0;
+  int64_t tab_bytes = 0;
   std::mutex mu;
 };
 
@@ -42,9 +43,10 @@ double log_pow2m1(int a) { return a * std::log(2.0) + std::log1p(-std::ldexp(1.0
 // query-order tables
 // ---------------------------------------------------------------------------
 struct HostTables {
-  std::vector<uint64_t> pat;
-  std::vector<int32_t> sbase, lbase, lnum, lcnt, loff;
-  int wtop = 0, nm = 1, jmax = 1;
+  std::vector<uint4> ent;       // weight byte + rank bytes, per (c, class) order, concatenated
+  std::vector<uint16_t> cost;   // cost of each entry
+  std::vector<int32_t> base, count;
+  int ncls = 1, class_size = 0, jmax = 1;
 };
 
 // cnt[w][m] = number of w-subsets of {1..n} with sum m (saturating), w <= wlim
@@ -69,116 +71,122 @@ struct SubsetCounts {
   }
 };
 
-// append, in lexicographic order of the ascending rank vector, every
-// w-subset of {lo..n} with sum `rest` to the partial mask
-void emit_subsets(int n, int w, int lo, int64_t rest, uint64_t m0, uint64_t m1, int nm, std::vector<uint64_t> &out) {
-  if (w == 0) {
+// Append, in lexicographic order of the ascending rank vector, every subset
+// of {lo..n} with `left` more elements and sum `rest` (ranks 1-based here,
+// stored 0-based in bytes 1..w of the entry).
+void emit_subsets(int n, int w, int depth, int lo, int64_t rest, uint8_t *bytes, std::vector<uint4> &out) {
+  const int left = w - depth;
+  if (left == 0) {
     if (rest == 0) {
-      out.push_back(m0);
-      if (nm == 2) out.push_back(m1);
+      uint4 e;
+      std::memcpy(&e, bytes, 16);
+      out.push_back(e);
     }
     return;
   }
   for (int r = lo; r <= n; r++) {
-    const int64_t left = rest - r;
-    const int64_t k = w - 1;
-    if (left < k * r + k * (k + 1) / 2) break;       // the k smallest ranks above r already exceed it
-    if (left > k * n - k * (k - 1) / 2) continue;    // the k largest ranks cannot reach it
-    uint64_t a = m0, b = m1;
-    if (r <= 64)
-      a |= 1ull << (r - 1);
-    else
-      b |= 1ull << (r - 65);
-    emit_subsets(n, w - 1, r + 1, left, a, b, nm, out);
+    const int64_t rem = rest - r;
+    const int64_t k = left - 1;
+    if (rem < k * r + k * (k + 1) / 2) break;     // the k smallest ranks above r already exceed it
+    if (rem > k * n - k * (k - 1) / 2) continue;  // the k largest ranks cannot reach it
+    bytes[1 + depth] = (uint8_t)(r - 1);
+    emit_subsets(n, w, depth + 1, r + 1, rem, bytes, out);
   }
+  bytes[1 + depth] = 0;
 }
 
-int build_tables(int n, int64_t cap, int c_max, HostTables &T) {
+int build_tables(int n, int64_t cap, int c_max, bool even, HostTables &T) {
   const int wlim = std::min(n, sg::WMAXT - 1);
   SubsetCounts N(n, wlim);
-  T.nm = (n + 63) / 64;
-  // weights that can be reached within `cap` queries for some c >= 0
-  // (c = 0 reaches each weight earliest) in any parity class
+  const int ncls = even ? 2 : 1;
+  // weights reachable within `cap` queries for some c >= 0 (c = 0 reaches
+  // each weight earliest) in any class
   int wtop = 1;
-  for (int K = 0; K < 3; K++) {  // 0 even, 1 odd, 2 all
+  for (int K = 0; K < ncls; K++) {
     std::vector<int64_t> pre(N.M + 2, 0);
     for (int m = 0; m <= N.M; m++) {
       int64_t s = 0;
       for (int w = 0; w <= wlim; w++)
-        if (K == 2 || (w & 1) == K) s = sat_add(s, N.at(w, m));
+        if (!even || (w & 1) == K) s = sat_add(s, N.at(w, m));
       pre[m + 1] = sat_add(pre[m], s);
     }
     for (int w = 0; w <= wlim; w++) {
-      if (K != 2 && (w & 1) != K) continue;
+      if (even && (w & 1) != K) continue;
       if (pre[w * (w + 1) / 2] <= cap) wtop = std::max(wtop, w + 1);
     }
   }
-  T.wtop = wtop;
-  T.sbase.assign(wtop, 0);
-  T.lbase.assign(wtop, 0);
-  T.lnum.assign(wtop, 0);
-  int64_t total = 0;
+  if (wtop - 1 > sg::WENT) return SOGRAND_EUNSUPPORTED;
+  // per-weight streams: every w-subset in (logistic weight, lexicographic)
+  // order, complete levels while the level starts within the first `cap`
+  std::vector<std::vector<uint4>> stream(wtop);
+  std::vector<std::vector<int64_t>> loff(wtop);  // level start, indexed by m - mmin(w); one extra end entry
   for (int w = 0; w < wtop; w++) {
-    T.sbase[w] = (int32_t)total;
-    T.lbase[w] = (int32_t)T.lcnt.size();
     const int mlo = w * (w + 1) / 2, mhi = w * (2 * n - w + 1) / 2;
     int64_t off = 0;
+    uint8_t bytes[16] = {0};
+    bytes[0] = (uint8_t)w;
     for (int m = mlo; m <= mhi && off <= cap; m++) {
       const int64_t cnt = N.at(w, m);
-      if (cnt >= (int64_t(1) << 30) || off + cnt >= (int64_t(1) << 30)) return SOGRAND_ENOMEM;
-      T.lcnt.push_back((int32_t)cnt);
-      T.loff.push_back((int32_t)off);
-      const size_t before = T.pat.size();
-      emit_subsets(n, w, 1, m, 0ull, 0ull, T.nm, T.pat);
-      if ((int64_t)(T.pat.size() - before) != cnt * T.nm) return SOGRAND_EINVAL;  // internal consistency
+      if (off + cnt >= (int64_t(1) << 28)) return SOGRAND_ENOMEM;
+      loff[w].push_back(off);
+      emit_subsets(n, w, 0, 1, m, bytes, stream[w]);
       off += cnt;
+      if ((int64_t)stream[w].size() != off) return SOGRAND_EINVAL;  // internal consistency
     }
-    T.lnum[w] = (int32_t)(T.lcnt.size() - T.lbase[w]);
-    total += off;
-    if (total >= (int64_t(1) << 27)) return SOGRAND_ENOMEM;
+    loff[w].push_back(off);
   }
-  // largest cost level a search of at most `cap` queries can stop on
-  // (nondecreasing in c, so evaluated at c_max), per parity class
-  int64_t cmax_all = 0;
-  for (int K = 0; K < 3; K++) {
-    int64_t cum = 0, C = 0, last = 0;
-    const int64_t Ctop = (int64_t)c_max * n + (int64_t)n * (n + 1) / 2;
-    for (C = 0; C <= Ctop; C++) {
-      int64_t s = 0;
-      for (int w = 0; w < wtop; w++) {
-        if (K != 2 && (w & 1) != K) continue;
-        s = sat_add(s, N.at(w, C - (int64_t)c_max * w));
+  // merged order for every (c, class)
+  T.ncls = ncls;
+  const int nb = even ? n - 1 : n;
+  T.class_size = nb >= 31 ? INT32_MAX : (1 << nb);
+  T.base.assign((size_t)(c_max + 1) * ncls, 0);
+  T.count.assign((size_t)(c_max + 1) * ncls, 0);
+  int maxcost = 0;
+  for (int c = 0; c <= c_max; c++) {
+    for (int K = 0; K < ncls; K++) {
+      const size_t start = T.ent.size();
+      const int64_t Ctop = (int64_t)c * n + (int64_t)n * (n + 1) / 2;
+      for (int64_t C = 0; C <= Ctop && (int64_t)(T.ent.size() - start) < cap; C++) {
+        for (int w = 0; w < wtop; w++) {
+          if (even && (w & 1) != K) continue;
+          const int64_t m = C - (int64_t)c * w;
+          const int64_t mlo = w * (w + 1) / 2;
+          if (m < mlo) break;
+          const int64_t li = m - mlo;
+          if (li + 1 >= (int64_t)loff[w].size()) continue;  // past the stored levels (beyond the cap)
+          const int64_t a = loff[w][li], b = loff[w][li + 1];
+          if (b == a) continue;
+          if (C > 65535) return SOGRAND_EUNSUPPORTED;
+          T.ent.insert(T.ent.end(), stream[w].begin() + a, stream[w].begin() + b);
+          T.cost.insert(T.cost.end(), (size_t)(b - a), (uint16_t)C);
+          maxcost = std::max(maxcost, (int)C);
+        }
+        if (T.ent.size() >= (size_t(1) << 30)) return SOGRAND_ENOMEM;
       }
-      if (s) last = C;
-      cum = sat_add(cum, s);
-      if (cum >= cap) break;
+      T.base[(size_t)c * ncls + K] = (int32_t)start;
+      T.count[(size_t)c * ncls + K] = (int32_t)(T.ent.size() - start);
     }
-    cmax_all = std::max(cmax_all, std::min(C, Ctop) > last ? std::min(C, Ctop) : last);
   }
-  if (cmax_all > 60000) return SOGRAND_ENOMEM;
-  T.jmax = (int)cmax_all + 2;
+  T.jmax = maxcost + 2;
   return SOGRAND_OK;
 }
 
 int upload_tables(sogrand_code *c, const HostTables &T, int64_t cap) {
-  const size_t bpat = T.pat.size() * sizeof(uint64_t);
-  const size_t nw = T.sbase.size(), nl = T.lcnt.size();
-  const size_t bint = (3 * nw + 2 * nl) * sizeof(int32_t);
-  const size_t bytes = ((bpat + 255) & ~size_t(255)) + bint + 16;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t be = T.ent.size() * sizeof(uint4), bc = T.cost.size() * sizeof(uint16_t);
+  const size_t bi = T.base.size() * sizeof(int32_t);
+  const size_t bytes = al(be) + al(bc) + 2 * al(bi);
   void *mem = nullptr;
   if (cudaMalloc(&mem, bytes) != cudaSuccess) return SOGRAND_ENOMEM;
   char *p = (char *)mem;
-  uint64_t *dpat = (uint64_t *)p;
-  int32_t *di = (int32_t *)(p + ((bpat + 255) & ~size_t(255)));
-  std::vector<int32_t> ints;
-  ints.reserve(3 * nw + 2 * nl);
-  ints.insert(ints.end(), T.sbase.begin(), T.sbase.end());
-  ints.insert(ints.end(), T.lbase.begin(), T.lbase.end());
-  ints.insert(ints.end(), T.lnum.begin(), T.lnum.end());
-  ints.insert(ints.end(), T.lcnt.begin(), T.lcnt.end());
-  ints.insert(ints.end(), T.loff.begin(), T.loff.end());
-  if ((bpat && cudaMemcpy(dpat, T.pat.data(), bpat, cudaMemcpyHostToDevice) != cudaSuccess) ||
-      cudaMemcpy(di, ints.data(), ints.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+  uint4 *dent = (uint4 *)p;
+  uint16_t *dcost = (uint16_t *)(p + al(be));
+  int32_t *dbase = (int32_t *)(p + al(be) + al(bc));
+  int32_t *dcount = (int32_t *)(p + al(be) + al(bc) + al(bi));
+  if (cudaMemcpy(dent, T.ent.data(), be, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dcost, T.cost.data(), bc, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dbase, T.base.data(), bi, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dcount, T.count.data(), bi, cudaMemcpyHostToDevice) != cudaSuccess) {
     cudaFree(mem);
     return SOGRAND_ECUDA;
   }
@@ -187,16 +195,15 @@ int upload_tables(sogrand_code *c, const HostTables &T, int64_t cap) {
     cudaFree(c->d_tab);
   }
   c->d_tab = mem;
-  c->tab.pat = dpat;
-  c->tab.sbase = di;
-  c->tab.lbase = di + nw;
-  c->tab.lnum = di + 2 * nw;
-  c->tab.lcnt = di + 3 * nw;
-  c->tab.loff = di + 3 * nw + nl;
-  c->tab.wtop = T.wtop;
-  c->tab.nm = T.nm;
+  c->ord.ent = dent;
+  c->ord.cost = dcost;
+  c->ord.base = dbase;
+  c->ord.count = dcount;
+  c->ord.ncls = T.ncls;
+  c->ord.class_size = T.class_size;
   c->jmax = T.jmax;
   c->tab_cap = cap;
+  c->tab_bytes = (int64_t)bytes;
   return SOGRAND_OK;
 }
 
@@ -205,7 +212,7 @@ int reserve_locked(sogrand_code *c, int64_t cap) {
   HostTables T;
   int rc;
   try {
-    rc = build_tables(c->n, cap, c->c_max, T);
+    rc = build_tables(c->n, cap, c->c_max, c->even != 0, T);
   } catch (const std::bad_alloc &) {
     return SOGRAND_ENOMEM;
   }
@@ -223,7 +230,7 @@ sg::DevCode dev_code(const sogrand_code *c) {
   d.log_phi = c->log_phi;
   d.hcol = c->d_hcol;
   d.hrow = c->d_hrow;
-  d.tab = c->tab;
+  d.ord = c->ord;
   d.jmax = c->jmax;
   return d;
 }
@@ -405,7 +412,10 @@ int sogrand_decode(sogrand_code *c, int64_t n_words, const float *llr_ch, const 
 
 int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L, int64_t cap,
                       float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status,
-                      int64_t *queries, int64_t *par_queries, int32_t *xf_words, void *stream) {
+                      int64_t *queries, product_decode_stats *stats, void *stream) {
+  int64_t *par_queries = stats ? stats->par_queries : nullptr;
+  if (stats && stats->timing_ms) stats->timing_ms[0] = stats->timing_ms[1] = 0.f;
+  if (stats && stats->launches) stats->launches[0] = 0;
   if (!rc_ || !cc_ || F < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f) ||
       !(alpha > 0.f && alpha < 1e6f) || max_iter < 1 || max_iter > 1000)
     return SOGRAND_EINVAL;
@@ -450,33 +460,92 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   a.par_queries = par_queries ? par_queries : (int64_t *)take(b_i64);
   a.status = status ? status : (uint8_t *)take((size_t)F);
   a.active = (int32_t *)take(sizeof(int32_t));
-  a.xf_count = xf_words;
+  a.xf_count = stats ? stats->xf_words : nullptr;
+  a.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
   sg::DevCode d = dev_code(c);
   sg::SisoParams P{L, (int32_t)cap, thr};
   cudaError_t e = cudaSuccess;
-  SG_DISPATCH(c, e = (sg::launch_product_init<NPL, SYN>(d, a, s)));
+  const bool timed = stats && stats->timing_ms;
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  if (timed)
+    for (int i = 0; i < 3 && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
+  int launches = 0;
+  float t_half = 0.f, t_check = 0.f;
+  if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_init<NPL, SYN>(d, a, s)));
   for (int h = 1; h <= a.max_half && e == cudaSuccess; h++) {
-    SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, P, a, h, s)));
+    if (timed) e = cudaEventRecord(ev[0], s);
+    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, P, a, h, s)));
     if (e != cudaSuccess) break;
-    e = cudaMemsetAsync(a.active, 0, sizeof(int32_t), s);
+    launches++;
+    if (timed) e = cudaEventRecord(ev[1], s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(a.active, 0, sizeof(int32_t), s);
+    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, a, h, s)));
     if (e != cudaSuccess) break;
-    SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, a, h, s)));
-    if (e != cudaSuccess) break;
+    launches++;
+    if (timed) e = cudaEventRecord(ev[2], s);
     int32_t act = 1;
-    e = cudaMemcpyAsync(&act, a.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&act, a.active, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && timed) {
+      float x = 0.f, y = 0.f;
+      e = cudaEventElapsedTime(&x, ev[0], ev[1]);
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&y, ev[1], ev[2]);
+      t_half += x;
+      t_check += y;
+    }
     if (e == cudaSuccess && act == 0) break;
   }
+  for (int i = 0; i < 3; i++)
+    if (ev[i]) cudaEventDestroy(ev[i]);
   cudaError_t e2 = cudaFreeAsync(mem, s);
+  if (stats && stats->timing_ms) {
+    stats->timing_ms[0] = t_half;
+    stats->timing_ms[1] = t_check;
+  }
+  if (stats && stats->launches) stats->launches[0] = launches;
   if (e != cudaSuccess || e2 != cudaSuccess) return SOGRAND_ECUDA;
   return SOGRAND_OK;
+}
+
+int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
+                        int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                        uint8_t *status, int64_t *queries, void *stream) {
+  if (!rc_ || F < 0) return SOGRAND_EINVAL;
+  if (F == 0) return SOGRAND_OK;
+  if (!llr_ch || !bits) return SOGRAND_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = rc_->n;
+  const size_t b_in = (size_t)F * n * n * sizeof(float), nb = ((size_t)n * n + 7) / 8, b_bits = (size_t)F * nb;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t total = al(b_in) + al(b_bits) + al((size_t)F * 4) + al((size_t)F) + al((size_t)F * 8);
+  char *mem = nullptr;
+  if (cudaMallocAsync((void **)&mem, total, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  float *d_in = (float *)mem;
+  uint8_t *d_bits = (uint8_t *)(mem + al(b_in));
+  int32_t *d_hi = (int32_t *)(mem + al(b_in) + al(b_bits));
+  uint8_t *d_st = (uint8_t *)(mem + al(b_in) + al(b_bits) + al((size_t)F * 4));
+  int64_t *d_q = (int64_t *)(mem + al(b_in) + al(b_bits) + al((size_t)F * 4) + al((size_t)F));
+  int rc = SOGRAND_OK;
+  if (cudaMemcpyAsync(d_in, llr_ch, b_in, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = SOGRAND_ECUDA;
+  if (rc == SOGRAND_OK)
+    rc = product_decode_ex(rc_, cc_, F, d_in, L, cap, thr, alpha, max_iter, d_bits, d_hi, d_st, d_q, nullptr, stream);
+  if (rc == SOGRAND_OK) {
+    cudaError_t e = cudaMemcpyAsync(bits, d_bits, b_bits, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && half_iters) e = cudaMemcpyAsync(half_iters, d_hi, (size_t)F * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, d_st, (size_t)F, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess && queries) e = cudaMemcpyAsync(queries, d_q, (size_t)F * 8, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) rc = SOGRAND_ECUDA;
+  }
+  if (cudaFreeAsync(mem, s) != cudaSuccess && rc == SOGRAND_OK) rc = SOGRAND_ECUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == SOGRAND_OK) rc = SOGRAND_ECUDA;
+  return rc;
 }
 
 int product_decode(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch, int L,
                    int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
                    uint8_t *status, int64_t *queries, void *stream) {
   return product_decode_ex(row_code, col_code, n_frames, llr_ch, L, cap, thr, alpha, max_iter, bits, half_iters,
-                           status, queries, nullptr, nullptr, stream);
+                           status, queries, nullptr, stream);
 }
 
 int sogrand_trace_patterns(sogrand_code *c, const float *llr, int64_t max_q, uint64_t *patterns_out, int64_t *n_out,
@@ -512,5 +581,17 @@ int sogrand_trace_patterns(sogrand_code *c, const float *llr, int64_t max_q, uin
   if (c_out) *c_out = h[1];
   return SOGRAND_OK;
 }
+
+#ifdef SG_PHASE_PROFILE
+// phase counters of the profiling build (not part of the public ABI)
+int sogrand_debug_phase(unsigned long long *out, int reset) {
+  cudaError_t e = cudaMemcpyFromSymbol(out, sg::g_phase, sizeof(unsigned long long) * 16);
+  if (reset) {
+    unsigned long long z[16] = {0};
+    cudaMemcpyToSymbol(sg::g_phase, z, sizeof(z));
+  }
+  return e == cudaSuccess ? 0 : SOGRAND_ECUDA;
+}
+#endif
 
 }  // extern "C"

@@ -26,7 +26,7 @@ __host__ __device__ inline int warp_scratch_bytes(int jmax) {
 
 // ---------------------------------------------------------------------------
 template <int NPL, class SYN>
-__global__ void __launch_bounds__(TPB) k_decode(const DevCode code, const SisoParams P, const DecodeArgs a,
+__global__ void __launch_bounds__(TPB, 4) k_decode(const DevCode code, const SisoParams P, const DecodeArgs a,
                                                 int wbytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NM = (32 * NPL + 63) / 64;
@@ -67,6 +67,7 @@ __global__ void __launch_bounds__(TPB) k_decode(const DevCode code, const SisoPa
       if (a.queries) a.queries[w] = res.queries;
       if (a.list_count) a.list_count[w] = res.nhit;
       if (used_xf && a.xf_count) atomicAdd(a.xf_count, 1);
+      if (a.wsum) atomicAdd(a.wsum, (unsigned long long)res.wsum);
     }
     if (a.list_words || a.list_app) {
       for (int l = lane; l < P.L; l += 32) {
@@ -74,7 +75,7 @@ __global__ void __launch_bounds__(TPB) k_decode(const DevCode code, const SisoPa
 #pragma unroll
           for (int wd = 0; wd < NM; wd++)
             a.list_words[((size_t)w * P.L + l) * NM + wd] = l < res.nhit ? sc.cw[l * NM + wd] : 0ull;
-        if (a.list_app) a.list_app[(size_t)w * P.L + l] = l < res.nhit ? expf(sc.lp[l] - res.logD) : 0.f;
+        if (a.list_app) a.list_app[(size_t)w * P.L + l] = l < res.nhit ? sc.wl[l] : 0.f;
       }
     }
     __syncwarp();
@@ -104,7 +105,7 @@ __global__ void k_trace(const DevCode code, const float *lam_in, int max_q, uint
 enum : int32_t { F_RUN = 0, F_DECODED = 1, F_MAXIT = 2, F_BAD_PENDING = 3, F_BAD = 4 };
 
 template <int NPL, class SYN, bool ROWS>
-__global__ void __launch_bounds__(TPB) k_product_half(const DevCode code, const SisoParams P, const ProductArgs a,
+__global__ void __launch_bounds__(TPB, 4) k_product_half(const DevCode code, const SisoParams P, const ProductArgs a,
                                                       int half, int wbytes) {
   extern __shared__ __align__(16) unsigned char smem[];
   constexpr int NM = (32 * NPL + 63) / 64;
@@ -159,6 +160,7 @@ __global__ void __launch_bounds__(TPB) k_product_half(const DevCode code, const 
       } else {
         atomicAdd(reinterpret_cast<unsigned long long *>(a.queries + f), (unsigned long long)res.queries);
         atomicMax(a.hmax + f, res.queries);
+        if (a.wsum) atomicAdd(a.wsum, (unsigned long long)res.wsum);
       }
       if (used_xf && a.xf_count) atomicAdd(a.xf_count, 1);
     }

@@ -23,6 +23,7 @@ struct DecodeArgs {
   float *list_app;       // [W][L]
   int32_t *list_count;   // [W]
   int32_t *xf_count;     // [1] words that needed the extended-range remainder (diagnostic)
+  unsigned long long *wsum;  // [1] += summed pattern weights of all queries (may be null)
 };
 
 // Block-turbo decoding of product codes (plain form: one launch per half).
@@ -42,6 +43,7 @@ struct ProductArgs {
   int64_t *par_queries;  // [F] out ("parallelized": sum over halves of the per-half max)
   int32_t *active;       // [1] frames still running after the last check (scratch, may be null)
   int32_t *xf_count;
+  unsigned long long *wsum;  // [1] += summed pattern weights of all queries (may be null)
 };
 
 template <int NPL, class SYN>

@@ -1,29 +1,31 @@
 // sg_common.h -- types shared by the host and device halves of libsogrand.
 // Internal to the library; the public interface is include/sogrand.h.
 #pragma once
+#include <cuda_runtime.h>
+
 #include <cstdint>
 
 namespace sg {
 
 constexpr int NMAX = 128;      // longest component code
 constexpr int LMAX = 16;       // longest list a decode may request
-constexpr int WMAXT = 64;      // most Hamming-weight streams a pattern table holds
+constexpr int WMAXT = 64;      // most Hamming weights a query-order table may reach
+constexpr int WENT = 15;       // most ranks one table entry holds
 constexpr int WARPS_PER_BLOCK = 4;
 
-// Query-order tables of one code length (built on the host, resident on the
-// device).  Stream w holds every w-subset of the reliability ranks {1..n}
-// in increasing logistic weight (sum of ranks) and, within one logistic
-// weight, in lexicographic order of the ascending rank vector, truncated
-// after the first level whose offset exceeds the query cap it was built for.
-struct DevTables {
-  const uint64_t *pat;   // [total][nm] rank masks (bit r-1 = rank r)
-  const int32_t *sbase;  // [wtop] first pattern of stream w
-  const int32_t *lbase;  // [wtop] first level record of stream w
-  const int32_t *lnum;   // [wtop] number of stored levels of stream w
-  const int32_t *lcnt;   // level sizes
-  const int32_t *loff;   // level offsets within the stream
-  int32_t wtop;          // streams 0..wtop-1 exist
-  int32_t nm;            // 64-bit words per mask
+// Query order of one code, flattened per 1-line parameter c and parity class.
+// For every c in [0, c_max] and class (the parity of y for an even code, or
+// the single class of all patterns) the patterns are stored in query order:
+// increasing cost = sum of ranks + c * weight, ties by weight, then by the
+// ascending rank vector in lexicographic order.  Each order is stored up to
+// the query cap it was built for and then to the end of that cost level.
+struct DevOrder {
+  const uint4 *ent;       // [total] byte 0: Hamming weight w; bytes 1..w: ranks (0-based, ascending)
+  const uint16_t *cost;   // [total] cost of each pattern
+  const int32_t *base;    // [(c_max+1) * ncls] first entry of order (c, class)
+  const int32_t *count;   // [(c_max+1) * ncls] entries stored for (c, class)
+  int32_t ncls;           // 2 for an even code (class = parity of y), else 1
+  int32_t class_size;     // patterns in one class (saturated): count == class_size means the whole class
 };
 
 struct DevCode {
@@ -33,8 +35,8 @@ struct DevCode {
   float log_phi;         // log((2^k-1)/(2^(n-1)-1)) (even) or log((2^k-1)/(2^n-1))
   const uint64_t *hcol;  // [n] syndrome contribution of bit i (bit t = H[t][i])
   const uint64_t *hrow;  // [m][nm] rows of H as bit masks over the n positions
-  DevTables tab;
-  int32_t jmax;          // largest cost level the remaining-mass DP may need, + 1
+  DevOrder ord;
+  int32_t jmax;          // largest stored cost + 2 (bounds the remaining-mass DP)
 };
 
 struct SisoParams {
@@ -49,6 +51,7 @@ struct WordResult {
   int32_t nhit;
   float pmiss;
   float logD;            // log(sum of list masses + R phi), relative to p(0)
+  int32_t wsum;          // sum of the Hamming weights of the queried patterns
 };
 
 }  // namespace sg

@@ -12,12 +12,13 @@
 //
 // Warp mapping: lane l holds bits l, l+32, ... (NPL per lane).  The word's
 // |lambda| are bitonic-sorted across the warp (64-bit keys |lambda|:index so
-// ties fall to the lower index), the H columns are permuted into rank order
-// in shared memory, and every chunk of 32 consecutive queries is spread over
-// the 32 lanes: lane j takes query q0 + j, XORs its pattern's H columns into
-// the syndrome of y and reports a hit; __ballot_sync + __ffs keep the hits in
-// query order, so list, stop point and query count are those of a sequential
-// decoder.
+// ties fall to the lower index) and the H columns are permuted into rank order
+// in shared memory.  The query order depends only on (n, c, parity class), so
+// it is read from a flattened table: every chunk of 32 consecutive queries is
+// one coalesced 512-byte load, lane j takes query q0 + j, XORs its pattern's
+// H columns into the syndrome of y and reports a hit; __ballot_sync + __ffs
+// keep the hits in query order, so list, stop point and query count are those
+// of a sequential decoder.
 //
 // Remaining mass.  The Corollary needs 1 - sum_{j <= q_L} p(z^j).  In FP32
 // that difference cancels catastrophically as soon as the queried mass
@@ -25,7 +26,7 @@
 // positive): patterns of cost above the stop level C* by a dynamic programme
 // over the ranks (cost-indexed, parity-split, a pattern is added to the tail
 // the moment one more rank lifts it over C*), plus the unqueried rest of
-// level C* by enumeration.  Masses are cost-scaled by exp(gamma * cost) so
+// level C* from the table.  Masses are cost-scaled by exp(gamma * cost) so
 // that every factor stays <= 1; if the scaled total still falls below 2^-60
 // (all dominant terms underflow) or overflows, the same computation is redone
 // in an extended-range float (FP32 mantissa + int exponent).
@@ -38,6 +39,15 @@
 #include "sg_common.h"
 
 namespace sg {
+
+#ifdef SG_PHASE_PROFILE
+// [0] prologue cycles [1] query-loop cycles [2] remainder cycles [3] soft-output
+// cycles [4] words [5] query chunks [6] - [7] DP ranks [8] XF fallbacks [9] smem DP
+__device__ unsigned long long g_phase[16];
+#define SG_PROF(i, v) atomicAdd(&g_phase[i], (unsigned long long)(v))
+#else
+#define SG_PROF(i, v) ((void)0)
+#endif
 
 constexpr unsigned FULL = 0xffffffffu;
 constexpr float LOG2E_F = 1.4426950408889634f;
@@ -80,12 +90,6 @@ __device__ __forceinline__ XF xf_from_log2(float x) {
   return xf_norm(exp2f(x - f), (int)f);
 }
 __device__ __forceinline__ float xf_log2(XF a) { return a.m == 0.f ? -CUDART_INF_F : (float)a.e + log2f(a.m); }
-__device__ __forceinline__ XF xf_shfl_down(XF a, int d) {
-  return {__shfl_down_sync(FULL, a.m, d), __shfl_down_sync(FULL, a.e, d)};
-}
-__device__ __forceinline__ XF xf_shfl_xor(XF a, int d) {
-  return {__shfl_xor_sync(FULL, a.m, d), __shfl_xor_sync(FULL, a.e, d)};
-}
 
 // Number policies for the remaining-mass computation.
 struct FOps {  // plain FP32, cost-scaled
@@ -94,8 +98,10 @@ struct FOps {  // plain FP32, cost-scaled
   static __device__ __forceinline__ T one() { return 1.f; }
   static __device__ __forceinline__ T add(T a, T b) { return a + b; }
   static __device__ __forceinline__ T mul(T a, T b) { return a * b; }
+  static __device__ __forceinline__ T fma(T a, T b, T c) { return fmaf(a, b, c); }
   static __device__ __forceinline__ T from_log2(float x) { return exp2f(x); }
   static __device__ __forceinline__ T from_float(float x) { return x; }
+  static __device__ __forceinline__ T shfl(T a, int src) { return __shfl_sync(FULL, a, src); }
   static __device__ __forceinline__ T shfl_down(T a, int d) { return __shfl_down_sync(FULL, a, d); }
   static __device__ __forceinline__ T shfl_xor(T a, int d) { return __shfl_xor_sync(FULL, a, d); }
 };
@@ -105,47 +111,62 @@ struct XOps {  // extended range, unscaled
   static __device__ __forceinline__ T one() { return xf_one(); }
   static __device__ __forceinline__ T add(T a, T b) { return xf_add(a, b); }
   static __device__ __forceinline__ T mul(T a, T b) { return xf_mul(a, b); }
+  static __device__ __forceinline__ T fma(T a, T b, T c) { return xf_add(xf_mul(a, b), c); }
   static __device__ __forceinline__ T from_log2(float x) { return xf_from_log2(x); }
   static __device__ __forceinline__ T from_float(float x) { return xf_norm(x, 0); }
-  static __device__ __forceinline__ T shfl_down(T a, int d) { return xf_shfl_down(a, d); }
-  static __device__ __forceinline__ T shfl_xor(T a, int d) { return xf_shfl_xor(a, d); }
+  static __device__ __forceinline__ T shfl(T a, int src) {
+    return {__shfl_sync(FULL, a.m, src), __shfl_sync(FULL, a.e, src)};
+  }
+  static __device__ __forceinline__ T shfl_down(T a, int d) {
+    return {__shfl_down_sync(FULL, a.m, d), __shfl_down_sync(FULL, a.e, d)};
+  }
+  static __device__ __forceinline__ T shfl_xor(T a, int d) {
+    return {__shfl_xor_sync(FULL, a.m, d), __shfl_xor_sync(FULL, a.e, d)};
+  }
 };
 
 // ----------------------------------------------------------------------------
 // per-warp shared-memory scratch
 // ----------------------------------------------------------------------------
+// H column and log2-mass of one reliability rank, read together in the query loop
+template <class SYN>
+struct RankRec {
+  SYN h;
+  float l2;
+};
+
 template <int NPL, class SYN>
 struct Layout {
   static constexpr int NT = 32 * NPL;
   static constexpr int NM = (NT + 63) / 64;
   static constexpr int o_l2 = 0;                                      // float[NT] |lambda| log2(e), by rank
   static constexpr int o_al = o_l2 + 4 * NT;                          // float[NT] |lambda|, by rank
-  static constexpr int o_hs = o_al + 4 * NT;                          // SYN[NT] H column, by rank
-  static constexpr int o_zm = align16(o_hs + (int)sizeof(SYN) * NT);  // u64[LMAX][NM] hit rank masks
-  static constexpr int o_cw = o_zm + 8 * LMAX * NM;                   // u64[LMAX][NM] hit codewords
+  static constexpr int o_hr = o_al + 4 * NT;                          // RankRec[NT] H column + log2 mass, by rank
+  static constexpr int o_cw = align16(o_hr + (int)sizeof(RankRec<SYN>) * NT);  // u64[LMAX][NM] listed codewords
   static constexpr int o_lp = o_cw + 8 * LMAX * NM;                   // float[LMAX] log p(z)/p(0)
-  static constexpr int o_perm = o_lp + 4 * LMAX;                      // u8[NT] rank -> bit
+  static constexpr int o_wl = o_lp + 4 * LMAX;                        // float[LMAX] APP of each listed word
+  static constexpr int o_perm = o_wl + 4 * LMAX;                      // u8[NT] rank -> bit
   static constexpr int o_tail = align16(o_perm + NT);
-  // tail area (sized for the 8-byte XF policy): sfac[NT], fu[NT+1], fb[NT+1], he[J], ho[J], ek[J]
-  static __host__ __device__ int bytes(int jm) { return align16(o_tail + 8 * (3 * NT + 2) + 20 * jm + 16); }
+  // tail area (sized for the 8-byte XF policy): sfac[NT+1], fu[NT+1], fb[NT+1], ek[J] (float), he[J], ho[J]
+  static __host__ __device__ int bytes(int jm) { return align16(o_tail + 24 * (NT + 1) + 20 * jm + 32); }
 };
 
 template <int NPL, class SYN>
 struct Scratch {
   using LY = Layout<NPL, SYN>;
   float *l2, *al;
-  SYN *hs;
-  uint64_t *zm, *cw;
-  float *lp;
+  RankRec<SYN> *hr;
+  uint64_t *cw;
+  float *lp, *wl;
   uint8_t *perm;
   unsigned char *tail;
   __device__ void bind(unsigned char *base) {
     l2 = reinterpret_cast<float *>(base + LY::o_l2);
     al = reinterpret_cast<float *>(base + LY::o_al);
-    hs = reinterpret_cast<SYN *>(base + LY::o_hs);
-    zm = reinterpret_cast<uint64_t *>(base + LY::o_zm);
+    hr = reinterpret_cast<RankRec<SYN> *>(base + LY::o_hr);
     cw = reinterpret_cast<uint64_t *>(base + LY::o_cw);
     lp = reinterpret_cast<float *>(base + LY::o_lp);
+    wl = reinterpret_cast<float *>(base + LY::o_wl);
     perm = base + LY::o_perm;
     tail = base + LY::o_tail;
   }
@@ -228,265 +249,152 @@ __device__ __forceinline__ int one_line_c(int64_t sy, int64_t sxy, int n, int c_
   return (int)(c > c_max ? c_max : c);
 }
 
-// ----------------------------------------------------------------------------
-// query-order walk over (cost level, Hamming weight) groups  (warp-uniform)
-// ----------------------------------------------------------------------------
-struct Walk {
-  DevTables T;
-  int n, c, w0, step, nw;
-  int C, wi, pos, gsize, gbase, a, b;
-  bool done;
+// rank k (0-based position in the pattern) of a table entry: byte k + 1
+template <int K>
+__device__ __forceinline__ int ent_rank(const uint4 &e) {
+  constexpr int B = K + 1;
+  const unsigned wd = (B >> 2) == 0 ? e.x : (B >> 2) == 1 ? e.y : (B >> 2) == 2 ? e.z : e.w;
+  return (wd >> (8 * (B & 3))) & 0xff;
+}
 
-  __device__ __forceinline__ int wt(int i) const { return w0 + i * step; }
-  __device__ __forceinline__ int lo(int i) const {
-    int w = wt(i);
-    return w * (w + 1) / 2 + c * w;
+// XOR of the rank-ordered H columns of a pattern and the sum of its ranks'
+// log2 masses (the loop runs to the warp's largest weight; shorter patterns
+// mask the extra terms)
+template <class SYN>
+__device__ __forceinline__ SYN ent_syndrome(const uint4 &e, int w, int wmax, const RankRec<SYN> *hr, float &l2sum) {
+  SYN s = 0;
+  float m = 0.f;
+#define SG_R(K)                                    \
+  if (K < wmax) {                                  \
+    const RankRec<SYN> v = hr[ent_rank<K>(e)];     \
+    const bool on = K < w;                         \
+    s ^= on ? v.h : (SYN)0;                        \
+    m += on ? v.l2 : 0.f;                          \
   }
-  __device__ __forceinline__ int hi(int i) const {
-    int w = wt(i);
-    return w * (2 * n - w + 1) / 2 + c * w;
-  }
-  __device__ __forceinline__ void load() {
-    int w = wt(wi);
-    int li = C - c * w - w * (w + 1) / 2;
-    if (li < 0 || li >= __ldg(T.lnum + w)) {
-      gsize = 0;
-      gbase = 0;
-    } else {
-      int base = __ldg(T.lbase + w) + li;
-      gsize = __ldg(T.lcnt + base);
-      gbase = __ldg(T.sbase + w) + __ldg(T.loff + base);
-    }
-    pos = 0;
-  }
-  __device__ __forceinline__ void settle() {
-    for (;;) {
-      while (a < nw && hi(a) < C) a++;
-      while (b + 1 < nw && lo(b + 1) <= C) b++;
-      if (a <= b) break;
-      if (b + 1 < nw) {
-        C = lo(b + 1);
-        continue;
-      }
-      done = true;
-      return;
-    }
-    wi = a;
-    load();
-  }
-  __device__ void init(const DevTables &t, int n_, int c_, bool even, int par) {
-    T = t;
-    n = n_;
-    c = c_;
-    w0 = even ? par : 0;
-    step = even ? 2 : 1;
-    int top = t.wtop < n + 1 ? t.wtop : n + 1;
-    nw = top > w0 ? (top - w0 + step - 1) / step : 0;
-    a = 0;
-    b = -1;
-    done = nw == 0;
-    if (!done) {
-      C = lo(0);
-      settle();
-    }
-  }
-  __device__ __forceinline__ void advance() {
-    if (wi < b) {
-      wi++;
-      load();
-      return;
-    }
-    C++;
-    settle();
-  }
-  // jump to group (C_, wi_) with pos_ patterns of it already consumed
-  __device__ void seek(int C_, int wi_, int pos_) {
-    C = C_;
-    a = 0;
-    b = -1;
-    done = false;
-    while (a < nw && hi(a) < C) a++;
-    while (b + 1 < nw && lo(b + 1) <= C) b++;
-    wi = wi_;
-    load();
-    pos = pos_;
-  }
-  // Hand the next patterns (at most `limit`, and only of level Cfix when
-  // Cfix >= 0) to lanes 0..count-1.  Lane j receives its pattern index and
-  // the walk position just after it.
-  __device__ __forceinline__ int assign(int limit, int lane, int Cfix, int &pidx, int &lC, int &lwi, int &lpos) {
-    int base = 0;
-    while (base < limit && !done) {
-      if (Cfix >= 0 && C != Cfix) break;
-      int take = gsize - pos;
-      if (take > limit - base) take = limit - base;
-      int rel = lane - base;
-      if (rel >= 0 && rel < take) {
-        pidx = gbase + pos + rel;
-        lC = C;
-        lwi = wi;
-        lpos = pos + rel + 1;
-      }
-      base += take;
-      pos += take;
-      if (pos >= gsize) advance();
-    }
-    return base;
-  }
-};
+  SG_R(0) SG_R(1) SG_R(2) SG_R(3) SG_R(4) SG_R(5) SG_R(6) SG_R(7)
+  SG_R(8) SG_R(9) SG_R(10) SG_R(11) SG_R(12) SG_R(13) SG_R(14)
+#undef SG_R
+  l2sum = m;
+  return s;
+}
 
-template <int NM>
-__device__ __forceinline__ void load_mask(const DevTables &T, int pidx, uint64_t (&mk)[NM]) {
-  const uint64_t *p = T.pat + (size_t)pidx * NM;
-  if (NM == 1) {
-    mk[0] = __ldg(p);
-  } else {
-    ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2 *>(p));
-    mk[0] = v.x;
-    mk[NM - 1] = v.y;
-  }
+// sum over the pattern's ranks of a per-rank float
+__device__ __forceinline__ float ent_sum(const uint4 &e, int w, const float *x) {
+  float s = 0.f;
+#define SG_S(K) \
+  if (K < w) s += x[ent_rank<K>(e)];
+  SG_S(0) SG_S(1) SG_S(2) SG_S(3) SG_S(4) SG_S(5) SG_S(6) SG_S(7)
+  SG_S(8) SG_S(9) SG_S(10) SG_S(11) SG_S(12) SG_S(13) SG_S(14)
+#undef SG_S
+  return s;
 }
 
 // ----------------------------------------------------------------------------
 // remaining mass: tail over cost > Cs (DP) + unqueried rest of level Cs
 // ----------------------------------------------------------------------------
-// Returns the (scaled) remaining mass summed over the warp.  With FOps the
-// masses carry the factor 2^(g2 * Cs) (g2 = gamma log2 e); with XOps g2 = 0.
-template <class Ops, int NPL, class SYN>
-__device__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, Walk W, int n, int cls, int Cs, int wis,
-                                            int poss, float g2, int lane) {
+// Register form of the rank DP for Cs < 32 * SLOTS: lane l holds the head
+// masses of cost j = 32 s + l (s < SLOTS) for both parities; the shift by
+// d_e = e + 1 + c is a shuffle from lane (l - d) mod 32 plus a slot select.
+template <class Ops, int SLOTS>
+__device__ __forceinline__ void dp_regs(int Cs, int c, int R0, int cls, const typename Ops::T *sfac,
+                                        const typename Ops::T *fu, const typename Ops::T *fb, const float *ek,
+                                        typename Ops::T g_even, typename Ops::T g_odd, int lane,
+                                        typename Ops::T &acc) {
   using T = typename Ops::T;
-  constexpr int NT = 32 * NPL;
-  constexpr int NM = (NT + 63) / 64;
-  const int c = W.c;
-  T *sfac = reinterpret_cast<T *>(sc.tail);
-  T *fu = sfac + NT;
-  T *fb = fu + NT + 1;
-  T *he = fb + NT + 1;
-  T *ho = he + (Cs + 1);
-  float *ek = reinterpret_cast<float *>(ho + (Cs + 1));
   constexpr bool SCALED = sizeof(T) == 4;
-  const int R0 = min(max(Cs - c, 0), n);  // ranks e < R0 can sit inside a pattern of cost <= Cs
-  const float g2Cs = g2 * (float)Cs;
-
-  // --- unqueried rest of level Cs
-  T acc = Ops::zero();
-  {
-    Walk R = W;
-    R.seek(Cs, wis, poss);
-    if (R.pos >= R.gsize) R.advance();
-    while (!R.done && R.C == Cs) {
-      int pidx = 0, lC, lwi, lpos;
-      int cnt = R.assign(32, lane, Cs, pidx, lC, lwi, lpos);
-      if (lane < cnt) {
-        uint64_t mk[NM];
-        load_mask<NM>(W.T, pidx, mk);
-        float s2 = 0.f;
+  T he[SLOTS], ho[SLOTS];
 #pragma unroll
-        for (int wd = 0; wd < NM; wd++) {
-          uint64_t x = mk[wd];
-          while (x) {
-            int r = __ffsll((long long)x) - 1 + 64 * wd;
-            x &= x - 1;
-            s2 += sc.l2[r];
-          }
-        }
-        acc = Ops::add(acc, Ops::from_log2(g2Cs - s2));
-      }
-      if (cnt == 0) break;
-    }
+  for (int t = 0; t < SLOTS; t++) {
+    he[t] = (t == 0 && lane == 0) ? Ops::one() : Ops::zero();
+    ho[t] = Ops::zero();
   }
-
-  // --- per-rank factors and suffix products F_e = prod_{e' >= e} (1 + y t_e')
-  //     kept as (u, b) = (even part - 1, odd part); lanes own ranks
-  //     lane*NPL .. lane*NPL+NPL-1.
-  {
-    T lu[NPL], lb[NPL];
-    T u = Ops::zero(), b = Ops::zero();
+  for (int e = 0; e < R0; e++) {
+    const int d = e + 1 + c;
+    const T s = sfac[e];
+    const T Fb = fb[e + 1];
+    const T F1u = Ops::add(Ops::one(), fu[e + 1]);
+    const int dq = d >> 5, dr = d & 31;
+    const int src = (lane - dr) & 31;
+    const int back = dq + (lane < dr ? 1 : 0);  // source slot = sl - back
+    T she[SLOTS], sho[SLOTS];
 #pragma unroll
-    for (int k = NPL - 1; k >= 0; k--) {
-      int e = lane * NPL + k;
-      T t = Ops::zero();
-      if (e < n) {
-        t = Ops::from_log2(-sc.l2[e]);
-        // factor used by the tail: low ranks t * 2^(g2 d_e), high ranks t * 2^(g2 Cs)
-        float d = (float)(e + 1 + c);
-        sfac[e] = Ops::from_log2((e < R0 ? g2 * d : g2Cs) - sc.l2[e]);
-      }
-      T nu = Ops::add(u, Ops::mul(b, t));
-      T nb = Ops::add(Ops::add(b, t), Ops::mul(u, t));
-      u = nu;
-      b = nb;
-      lu[k] = u;
-      lb[k] = b;
-    }
-    // inclusive suffix scan of the block products over lanes
-    T su = u, sb = b;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      T ou = Ops::shfl_down(su, d), ob = Ops::shfl_down(sb, d);
-      if (lane + d < 32) {
-        T nu = Ops::add(Ops::add(su, ou), Ops::add(Ops::mul(su, ou), Ops::mul(sb, ob)));
-        T nb = Ops::add(Ops::add(sb, ob), Ops::add(Ops::mul(su, ob), Ops::mul(sb, ou)));
-        su = nu;
-        sb = nb;
-      }
-    }
-    T xu = Ops::shfl_down(su, 1), xb = Ops::shfl_down(sb, 1);
-    if (lane == 31) {
-      xu = Ops::zero();
-      xb = Ops::zero();
+    for (int t = 0; t < SLOTS; t++) {
+      she[t] = Ops::shfl(he[t], src);
+      sho[t] = Ops::shfl(ho[t], src);
     }
 #pragma unroll
-    for (int k = 0; k < NPL; k++) {
-      int e = lane * NPL + k;
-      if (e <= n) {
-        T fu_ = Ops::add(Ops::add(lu[k], xu), Ops::add(Ops::mul(lu[k], xu), Ops::mul(lb[k], xb)));
-        T fb_ = Ops::add(Ops::add(lb[k], xb), Ops::add(Ops::mul(lu[k], xb), Ops::mul(lb[k], xu)));
-        if (e < n) {
-          fu[e] = fu_;
-          fb[e] = fb_;
+    for (int sl = 0; sl < SLOTS; sl++) {
+      const int j = sl * 32 + lane;
+      if (j <= Cs) {
+        if (j > Cs - d) {
+          T w = s;
+          if constexpr (SCALED) w = Ops::mul(w, Ops::from_float(ek[j + d - Cs]));
+          T term;
+          if (cls == 0)
+            term = Ops::add(Ops::mul(he[sl], Fb), Ops::mul(ho[sl], F1u));
+          else if (cls == 1)
+            term = Ops::add(Ops::mul(he[sl], F1u), Ops::mul(ho[sl], Fb));
+          else
+            term = Ops::mul(Ops::add(he[sl], ho[sl]), Ops::add(F1u, Fb));
+          acc = Ops::fma(w, term, acc);
+        }
+        if (j >= d) {
+          const int ss = sl - back;
+          T pe = Ops::zero(), po = Ops::zero();
+#pragma unroll
+          for (int t = 0; t < SLOTS; t++)
+            if (t == ss) {
+              pe = she[t];
+              po = sho[t];
+            }
+          he[sl] = Ops::fma(s, po, he[sl]);
+          ho[sl] = Ops::fma(s, pe, ho[sl]);
         }
       }
     }
-    if (lane == 0) {
-      fu[n] = Ops::zero();
-      fb[n] = Ops::zero();
+#ifdef SG_PHASE_PROFILE
+    if (lane == 0) SG_PROF(7, 1);
+#endif
+  }
+  // high ranks (d_e > Cs) joined to every head pattern
+#pragma unroll
+  for (int sl = 0; sl < SLOTS; sl++) {
+    const int j = sl * 32 + lane;
+    if (j <= Cs) {
+      T w = Ops::one();
+      if constexpr (SCALED) w = Ops::from_float(ek[j]);
+      T term;
+      if (cls == 0)
+        term = Ops::add(Ops::mul(he[sl], g_even), Ops::mul(ho[sl], g_odd));
+      else if (cls == 1)
+        term = Ops::add(Ops::mul(he[sl], g_odd), Ops::mul(ho[sl], g_even));
+      else
+        term = Ops::mul(Ops::add(he[sl], ho[sl]), Ops::add(g_even, g_odd));
+      acc = Ops::fma(w, term, acc);
     }
   }
-  // cost DP init and the 2^(-g2 k) table
+}
+
+// Shared-memory form of the same DP for large stop levels (out of line: rare).
+template <class Ops>
+__device__ __noinline__ void dp_smem(int Cs, int c, int R0, int cls, const typename Ops::T *sfac, const typename Ops::T *fu,
+                        const typename Ops::T *fb, const float *ek, typename Ops::T g_even, typename Ops::T g_odd,
+                        typename Ops::T *he, typename Ops::T *ho, int lane, typename Ops::T &acc) {
+  using T = typename Ops::T;
+  constexpr bool SCALED = sizeof(T) == 4;
   for (int j = lane; j <= Cs; j += 32) {
     he[j] = j == 0 ? Ops::one() : Ops::zero();
     ho[j] = Ops::zero();
-    if constexpr (SCALED) ek[j] = exp2f(-g2 * (float)j);
   }
   __syncwarp();
-
-  // --- high ranks (d_e > Cs): G_P = sum_e sfac_e * F_{e+1} (parity of
-  //     pattern {e} + higher subset), reduced over the warp
-  T g_even = Ops::zero(), g_odd = Ops::zero();
-  for (int e = R0 + lane; e < n; e += 32) {
-    T s = sfac[e];
-    T one_u = Ops::add(Ops::one(), fu[e + 1]);
-    g_odd = Ops::add(g_odd, Ops::mul(s, one_u));
-    g_even = Ops::add(g_even, Ops::mul(s, fb[e + 1]));
-  }
-#pragma unroll
-  for (int d = 16; d > 0; d >>= 1) {
-    g_even = Ops::add(g_even, Ops::shfl_xor(g_even, d));
-    g_odd = Ops::add(g_odd, Ops::shfl_xor(g_odd, d));
-  }
-
-  // --- low ranks in ascending order: tail contributions, then DP update.
-  //     Entry slots are walked from the top so that every read of
-  //     he/ho[j - d] sees the values before this rank (reads of a slot are
-  //     separated from its writes by __syncwarp).
   const int nslot = (Cs + 32) >> 5;
   for (int e = 0; e < R0; e++) {
     const int d = e + 1 + c;
     const T s = sfac[e];
     const T Fb = fb[e + 1];
     const T F1u = Ops::add(Ops::one(), fu[e + 1]);
+    // slots from the top, so every read of he/ho[j - d] sees the values
+    // before this rank (a slot's reads are separated from its writes)
     for (int sl = nslot - 1; sl >= 0; sl--) {
       const int j = sl * 32 + lane;
       T ne = Ops::zero(), no = Ops::zero();
@@ -504,11 +412,11 @@ __device__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, Walk W,
             term = Ops::add(Ops::mul(hej, F1u), Ops::mul(hoj, Fb));
           else
             term = Ops::mul(Ops::add(hej, hoj), Ops::add(F1u, Fb));
-          acc = Ops::add(acc, Ops::mul(w, term));
+          acc = Ops::fma(w, term, acc);
         }
         if (upd) {
-          ne = Ops::add(hej, Ops::mul(s, ho[j - d]));
-          no = Ops::add(hoj, Ops::mul(s, he[j - d]));
+          ne = Ops::fma(s, ho[j - d], hej);
+          no = Ops::fma(s, he[j - d], hoj);
         }
       }
       __syncwarp();
@@ -519,7 +427,6 @@ __device__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, Walk W,
       __syncwarp();
     }
   }
-  // high ranks joined to every head pattern
   for (int j = lane; j <= Cs; j += 32) {
     T w = Ops::one();
     if constexpr (SCALED) w = Ops::from_float(ek[j]);
@@ -530,7 +437,129 @@ __device__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, Walk W,
       term = Ops::add(Ops::mul(he[j], g_odd), Ops::mul(ho[j], g_even));
     else
       term = Ops::mul(Ops::add(he[j], ho[j]), Ops::add(g_even, g_odd));
-    acc = Ops::add(acc, Ops::mul(w, term));
+    acc = Ops::fma(w, term, acc);
+  }
+  __syncwarp();
+}
+
+// The (scaled) remaining mass summed over the warp.  With FOps every mass
+// carries the factor 2^(g2 * Cs) (g2 = gamma log2 e); with XOps g2 = 0.
+// `qs` is the order-table index of the last queried pattern.
+template <class Ops, int NPL, class SYN>
+__device__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs,
+                                            int n, int c, int cls, int Cs, float g2, int lane) {
+  using T = typename Ops::T;
+  constexpr int NT = 32 * NPL;
+  T *sfac = reinterpret_cast<T *>(sc.tail);
+  T *fu = sfac + NT + 1;
+  T *fb = fu + NT + 1;
+  float *ek = reinterpret_cast<float *>(fb + NT + 1);
+  T *he = reinterpret_cast<T *>(ek + align16(4 * (Cs + 1)) / 4);
+  T *ho = he + (Cs + 1);
+  constexpr bool SCALED = sizeof(T) == 4;
+  const int R0 = min(max(Cs - c, 0), n);  // ranks e < R0 can sit inside a pattern of cost <= Cs
+  const float g2Cs = g2 * (float)Cs;
+
+  // --- unqueried rest of level Cs (the table stores every level completely)
+  T acc = Ops::zero();
+  for (int q0 = qs + 1; q0 < tc; q0 += 32) {
+    const int q = q0 + lane;
+    bool in = false;
+    if (q < tc) in = __ldg(O.cost + tb + q) == (uint16_t)Cs;
+    if (in) {
+      const uint4 e = __ldg(O.ent + tb + q);
+      const float s2 = ent_sum(e, e.x & 0xff, sc.l2);
+      acc = Ops::add(acc, Ops::from_log2(g2Cs - s2));
+    }
+    if (!__all_sync(FULL, in)) break;  // costs are nondecreasing
+  }
+
+  // --- per-rank factors and suffix products F_e = prod_{e' >= e} (1 + y t_e')
+  //     kept as (u, b) = (even part - 1, odd part); lanes own ranks
+  //     lane*NPL .. lane*NPL+NPL-1.
+  {
+    T lu[NPL], lb[NPL];
+    T u = Ops::zero(), b = Ops::zero();
+#pragma unroll
+    for (int k = NPL - 1; k >= 0; k--) {
+      const int e = lane * NPL + k;
+      T t = Ops::zero();
+      if (e < n) {
+        t = Ops::from_log2(-sc.l2[e]);
+        // factor used by the tail: low ranks t * 2^(g2 d_e), high ranks t * 2^(g2 Cs)
+        const float d = (float)(e + 1 + c);
+        sfac[e] = Ops::from_log2((e < R0 ? g2 * d : g2Cs) - sc.l2[e]);
+      }
+      const T nu = Ops::fma(b, t, u);
+      const T nb = Ops::fma(u, t, Ops::add(b, t));
+      u = nu;
+      b = nb;
+      lu[k] = u;
+      lb[k] = b;
+    }
+    T su = u, sb = b;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const T ou = Ops::shfl_down(su, d), ob = Ops::shfl_down(sb, d);
+      if (lane + d < 32) {
+        const T nu = Ops::add(Ops::add(su, ou), Ops::fma(su, ou, Ops::mul(sb, ob)));
+        const T nb = Ops::add(Ops::add(sb, ob), Ops::fma(su, ob, Ops::mul(sb, ou)));
+        su = nu;
+        sb = nb;
+      }
+    }
+    T xu = Ops::shfl_down(su, 1), xb = Ops::shfl_down(sb, 1);
+    if (lane == 31) {
+      xu = Ops::zero();
+      xb = Ops::zero();
+    }
+#pragma unroll
+    for (int k = 0; k < NPL; k++) {
+      const int e = lane * NPL + k;
+      if (e < n) {
+        fu[e] = Ops::add(Ops::add(lu[k], xu), Ops::fma(lu[k], xu, Ops::mul(lb[k], xb)));
+        fb[e] = Ops::add(Ops::add(lb[k], xb), Ops::fma(lu[k], xb, Ops::mul(lb[k], xu)));
+      }
+    }
+    if (lane == 0) {
+      fu[n] = Ops::zero();
+      fb[n] = Ops::zero();
+    }
+  }
+  if constexpr (SCALED)
+    for (int j = lane; j <= Cs; j += 32) ek[j] = exp2f(-g2 * (float)j);
+  __syncwarp();
+
+  // --- high ranks (d_e > Cs): G_P = sum_e sfac_e * F_{e+1} (parity of the
+  //     pattern {e} + any higher subset), reduced over the warp
+  T g_even = Ops::zero(), g_odd = Ops::zero();
+  for (int e = R0 + lane; e < n; e += 32) {
+    const T s = sfac[e];
+    g_odd = Ops::fma(s, Ops::add(Ops::one(), fu[e + 1]), g_odd);
+    g_even = Ops::fma(s, fb[e + 1], g_even);
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    g_even = Ops::add(g_even, Ops::shfl_xor(g_even, d));
+    g_odd = Ops::add(g_odd, Ops::shfl_xor(g_odd, d));
+  }
+
+  // --- low ranks in ascending order: tail contributions and the cost DP
+  bool done = false;
+  if constexpr (SCALED) {
+    if (Cs < 64) {
+      dp_regs<Ops, 2>(Cs, c, R0, cls, sfac, fu, fb, ek, g_even, g_odd, lane, acc);
+      done = true;
+    } else if (Cs < 128) {
+      dp_regs<Ops, 4>(Cs, c, R0, cls, sfac, fu, fb, ek, g_even, g_odd, lane, acc);
+      done = true;
+    }
+  }
+  if (!done) {
+#ifdef SG_PHASE_PROFILE
+    if (lane == 0) SG_PROF(9, 1);
+#endif
+    dp_smem<Ops>(Cs, c, R0, cls, sfac, fu, fb, ek, g_even, g_odd, he, ho, lane, acc);
   }
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) acc = Ops::add(acc, Ops::shfl_xor(acc, d));
@@ -538,26 +567,71 @@ __device__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, Walk W,
   return acc;
 }
 
-// log2 of the remaining (unqueried) mass relative to p(0^n|r); warp-uniform.
+// Extended-range evaluation (out of line: only when every FP32-scaled term
+// of the dominant part underflows).
 template <int NPL, class SYN>
-__device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const Walk &W, int n, int cls, int Cs, int wis, int poss,
-                                int lane, int *used_xf) {
-  const int c = W.c;
+__device__ __noinline__ float remaining_log2_xf(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs,
+                                                int n, int c, int cls, int Cs, int lane) {
+  const XF x = remaining_scaled<XOps, NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, 0.f, lane);
+  return __shfl_sync(FULL, xf_log2(x), 0);
+}
+
+// log2 of the remaining (unqueried) mass relative to p(0^n|r); warp-uniform.
+// tq is the queried mass of the nonzero patterns (FP32, summed over the
+// warp).  When the class total minus tq is well conditioned (the difference
+// is at least 2% of the operands, so FP32 rounding of about 4e-6 of them
+// moves it by at most 2e-4 relative) that difference is used; otherwise the
+// unqueried patterns are summed directly.
+template <int NPL, class SYN>
+__device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs, int n, int c,
+                                int cls, int lane, float tq, int *used_xf) {
+  // class total of the nonzero patterns: prod_e (1 + y t_e) as (even - 1, odd)
+  {
+    float u = 0.f, b = 0.f;
+#pragma unroll
+    for (int k = 0; k < NPL; k++) {
+      const int e = lane * NPL + k;
+      if (e < n) {
+        const float t = exp2f(-sc.l2[e]);
+        const float nu = fmaf(b, t, u), nb = fmaf(u, t, b + t);
+        u = nu;
+        b = nb;
+      }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      const float ou = __shfl_xor_sync(FULL, u, d), ob = __shfl_xor_sync(FULL, b, d);
+      const float nu = (u + ou) + fmaf(u, ou, b * ob);
+      const float nb = (b + ob) + fmaf(u, ob, b * ou);
+      u = nu;
+      b = nb;
+    }
+    // the butterfly's fused products round differently per lane: take lane
+    // 0's value so the branch below is warp-uniform
+    u = __shfl_sync(FULL, u, 0);
+    b = __shfl_sync(FULL, b, 0);
+    const float enz = cls == 0 ? u : (cls == 1 ? b : u + b);
+    const float r = enz - tq;
+    if (enz > 1e-30f && enz < 1e30f && r > 0.02f * (enz + tq)) return log2f(r);
+  }
+  const int Cs = __ldg(O.cost + tb + qs);
   const int R0 = min(max(Cs - c, 0), n);
   float g = CUDART_INF_F;
   for (int e = lane; e < R0; e += 32) g = fminf(g, sc.l2[e] / (float)(e + 1 + c));
-  g = warp_min_f(g);
+  g = __shfl_sync(FULL, warp_min_f(g), 0);
   if (!(g < CUDART_INF_F)) g = 0.f;
-  float tot = remaining_scaled<FOps, NPL, SYN>(sc, W, n, cls, Cs, wis, poss, g, lane);
+  const float tot = __shfl_sync(FULL, remaining_scaled<FOps, NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, g, lane), 0);
   if (tot >= 0x1p-60f && tot < CUDART_INF_F) return log2f(tot) - g * (float)Cs;
   if (used_xf) *used_xf = 1;
-  XF x = remaining_scaled<XOps, NPL, SYN>(sc, W, n, cls, Cs, wis, poss, 0.f, lane);
-  return xf_log2(x);
+#ifdef SG_PHASE_PROFILE
+  if (lane == 0) SG_PROF(8, 1);
+#endif
+  return remaining_log2_xf<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, lane);
 }
 
 // numerically safe log(exp(a) + exp(b)) (natural log, -inf aware)
 __device__ __forceinline__ float lse(float a, float b) {
-  float mx = fmaxf(a, b), mn = fminf(a, b);
+  const float mx = fmaxf(a, b), mn = fminf(a, b);
   if (mx == -CUDART_INF_F) return mx;
   return mx + log1pf(expf(mn - mx));
 }
@@ -566,7 +640,6 @@ __device__ __forceinline__ float softplus(float z) { return fmaxf(z, 0.f) + log1
 // ----------------------------------------------------------------------------
 // one word
 // ----------------------------------------------------------------------------
-// Per-word state after the prologue (warp-uniform except yb).
 template <int NPL, class SYN>
 struct WordHead {
   unsigned yb[NPL];  // hard decision, bits lane + 32k
@@ -602,8 +675,8 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
   if (sizeof(SYN) == 4) {
     h.s0 = (SYN)__reduce_xor_sync(FULL, (unsigned)s0p);
   } else {
-    unsigned lo_ = __reduce_xor_sync(FULL, (unsigned)(uint64_t)s0p);
-    unsigned hi_ = __reduce_xor_sync(FULL, (unsigned)((uint64_t)s0p >> 32));
+    const unsigned lo_ = __reduce_xor_sync(FULL, (unsigned)(uint64_t)s0p);
+    const unsigned hi_ = __reduce_xor_sync(FULL, (unsigned)((uint64_t)s0p >> 32));
     h.s0 = (SYN)(((uint64_t)hi_ << 32) | lo_);
   }
 
@@ -625,7 +698,7 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
       sc.al[e] = a;
       sc.l2[e] = a * LOG2E_F;
       sc.perm[e] = (uint8_t)idx;
-      sc.hs[e] = (SYN)__ldg(code.hcol + idx);
+      sc.hr[e] = RankRec<SYN>{(SYN)__ldg(code.hcol + idx), a * LOG2E_F};
       const int64_t qa = quant256(a);
       sy += qa;
       sxy += qa * (e + 1);
@@ -638,39 +711,114 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
   return true;
 }
 
+// rank mask (bit r = rank r + 1) of a table entry
+template <int NM>
+__device__ __forceinline__ void ent_mask(const uint4 &e, uint64_t (&m)[NM]) {
+  const int w = e.x & 0xff;
+#pragma unroll
+  for (int x = 0; x < NM; x++) m[x] = 0;
+#define SG_M(K)                                           \
+  if (K < w) {                                            \
+    const int r = ent_rank<K>(e);                         \
+    _Pragma("unroll") for (int x = 0; x < NM; x++) {      \
+      if ((r >> 6) == x) m[x] |= 1ull << (r & 63);        \
+    }                                                     \
+  }
+  SG_M(0) SG_M(1) SG_M(2) SG_M(3) SG_M(4) SG_M(5) SG_M(6) SG_M(7)
+  SG_M(8) SG_M(9) SG_M(10) SG_M(11) SG_M(12) SG_M(13) SG_M(14)
+#undef SG_M
+}
+
 // The canonical query order for one input (test hook): writes the first
-// max_q rank masks; returns how many were written.
+// max_q rank masks (NM words each); returns how many were written.
 template <int NPL, class SYN>
 __device__ int trace_word(const DevCode &code, const Scratch<NPL, SYN> &sc, const float (&lam)[NPL], int lane,
                           int max_q, uint64_t *out, int *c_out) {
   constexpr int NM = (32 * NPL + 63) / 64;
   WordHead<NPL, SYN> h;
   if (!siso_prologue<NPL, SYN>(code, sc, lam, lane, h)) return -1;
-  Walk W;
-  W.init(code.tab, code.n, h.c, code.even != 0, h.par);
-  int q = 0;
-  while (!W.done && q < max_q) {
-    int limit = min(32, max_q - q);
-    int pidx = 0, lC, lwi, lpos;
-    const int nv = W.assign(limit, lane, -1, pidx, lC, lwi, lpos);
-    if (lane < nv) {
-      uint64_t mk[NM];
-      load_mask<NM>(code.tab, pidx, mk);
+  const DevOrder &O = code.ord;
+  const int ti = h.c * O.ncls + (code.even ? h.par : 0);
+  const int tb = __ldg(O.base + ti), tc = __ldg(O.count + ti);
+  const int qn = min(max_q, tc);
+  for (int q = lane; q < qn; q += 32) {
+    uint64_t m[NM];
+    ent_mask<NM>(__ldg(O.ent + tb + q), m);
 #pragma unroll
-      for (int wd = 0; wd < NM; wd++) out[(size_t)(q + lane) * NM + wd] = mk[wd];
-    }
-    q += nv;
-    if (nv == 0) break;
+    for (int x = 0; x < NM; x++) out[(size_t)q * NM + x] = m[x];
   }
   if (c_out && lane == 0) *c_out = h.c;
-  return q;
+  return qn;
+}
+
+__device__ __forceinline__ float warp_sum_f(float x) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(FULL, x, d);
+  return x;
+}
+
+// Record the hit of lane hl as list entry `slot`: the codeword y + z in bit
+// order (sc.cw) and log p(z)/p(0) = -sum |lambda| over z (sc.lp).  The
+// pattern is broadcast and lane k handles its k-th rank.
+template <int NPL, class SYN>
+__device__ __forceinline__ void record_hit(const Scratch<NPL, SYN> &sc, const WordHead<NPL, SYN> &h, const uint4 &e,
+                                           int hl, int slot, int lane) {
+  constexpr int NM = (32 * NPL + 63) / 64;
+  uint4 b;
+  b.x = __shfl_sync(FULL, e.x, hl);
+  b.y = __shfl_sync(FULL, e.y, hl);
+  b.z = __shfl_sync(FULL, e.z, hl);
+  b.w = __shfl_sync(FULL, e.w, hl);
+  const int w = b.x & 0xff;
+  const int byte = lane + 1;  // rank k = lane sits in byte k + 1
+  const unsigned wd = byte < 4 ? b.x : (byte < 8 ? b.y : (byte < 12 ? b.z : b.w));
+  const bool mine = lane < w;
+  const int r = mine ? (wd >> (8 * (byte & 3))) & 0xff : 0;
+  const float ls = warp_sum_f(mine ? sc.al[r] : 0.f);
+  const int bi = mine ? sc.perm[r] : 0;
+#pragma unroll
+  for (int k = 0; k < NPL; k++) {
+    const unsigned word = __reduce_or_sync(FULL, (mine && (bi >> 5) == k) ? 1u << (bi & 31) : 0u) ^ h.yb[k];
+    if (lane == 0) reinterpret_cast<unsigned *>(sc.cw + slot * NM)[k] = word;
+  }
+  if (lane == 0) {
+    if (NPL & 1) reinterpret_cast<unsigned *>(sc.cw + slot * NM)[NPL] = 0u;  // upper half of the last u64
+    sc.lp[slot] = -ls;
+  }
+  __syncwarp();
+}
+
+// threshold rule: predicted probability that the list misses the codeword
+__device__ __forceinline__ bool thr_reached(const float *lp, int nhit, float M, float thr) {
+  float D = M;
+  for (int l = 0; l < nhit; l++) D = lse(D, lp[l]);
+  return expf(M - D) < thr;
+}
+template <int NPL, class SYN>
+__device__ __forceinline__ bool thr_reached(const Scratch<NPL, SYN> &sc, int nhit, float M, float thr) {
+  return thr_reached(sc.lp, nhit, M, thr);
+}
+
+// eq. LLRi in the log domain for a bit whose linear sums underflowed (out of line: rare)
+template <int NPL, class SYN>
+__device__ __noinline__ float lapp_logdomain(const Scratch<NPL, SYN> &sc, int nhit, float M, float x, int i) {
+  constexpr int NM = (32 * NPL + 63) / 64;
+  float b0 = M - softplus(-x), b1 = M - softplus(x);
+  const uint64_t bitm = 1ull << (i & 63);
+  for (int l = 0; l < nhit; l++) {
+    if (sc.cw[l * NM + (i >> 6)] & bitm)
+      b1 = lse(b1, sc.lp[l]);
+    else
+      b0 = lse(b0, sc.lp[l]);
+  }
+  return b0 - b1;
 }
 
 // lam[k] is bit lane + 32k of the SISO input lambda = fl32(L_Ch + L_A)
 // (the caller loads it; entries past n are ignored).  On return lapp[k] holds
 // L_APP for the same bits, res the per-word results; the list (in query
-// order) is left in the scratch: sc.cw (codewords, natural bit order) and
-// sc.lp (log p(z)/p(0)).
+// order) is left in the scratch: sc.cw (codewords, natural bit order),
+// sc.lp (log p(z)/p(0)) and sc.wl (APP of each word).
 template <int NPL, class SYN>
 __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratch<NPL, SYN> &sc,
                           const float (&lam)[NPL], int lane, float (&lapp)[NPL], WordResult &res,
@@ -678,7 +826,9 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   constexpr int NT = 32 * NPL;
   constexpr int NM = (NT + 63) / 64;
   const int n = code.n;
-
+#ifdef SG_PHASE_PROFILE
+  const long long t0 = clock64();
+#endif
   WordHead<NPL, SYN> h;
   if (!siso_prologue<NPL, SYN>(code, sc, lam, lane, h)) {
 #pragma unroll
@@ -687,95 +837,54 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     res.nhit = 0;
     res.pmiss = 1.f;
     res.logD = 0.f;
+    res.wsum = 0;
     return;
   }
+#ifdef SG_PHASE_PROFILE
+  const long long t1 = clock64();
+  int nchunks = 0;
+#endif
 
-  // query loop
-  Walk W;
-  W.init(code.tab, n, h.c, code.even != 0, h.par);
+  // query loop over the flattened order of (c, class)
+  const DevOrder &O = code.ord;
   const int cls = code.even ? h.par : -1;
+  const int ti = h.c * O.ncls + (code.even ? h.par : 0);
+  const int tb = __ldg(O.base + ti), tc = __ldg(O.count + ti);
+  const int qlim = min(P.cap, tc);
   int q = 0, nhit = 0;
-  int sC = 0, swi = 0, spos = 0;
-  bool exhausted = false;
   float lr2 = 0.f;  // log2 remaining mass (set when the search stops)
   bool have_lr2 = false;
+  int wacc = 0;       // this lane's share of the summed pattern weights
+  float tmass = 0.f;  // this lane's share of the queried mass (nonzero patterns)
   for (;;) {
-    if (W.done) {
-      exhausted = true;
-      break;
-    }
-    int limit = P.cap - q;
-    if (limit > 32) limit = 32;
-    int pidx = 0, lC = 0, lwi = 0, lpos = 0;
-    const int nv = W.assign(limit, lane, -1, pidx, lC, lwi, lpos);
-    bool hit = false;
-    uint64_t mk[NM];
-#pragma unroll
-    for (int wd = 0; wd < NM; wd++) mk[wd] = 0;
-    if (lane < nv) {
-      load_mask<NM>(code.tab, pidx, mk);
-      SYN s = h.s0;
-#pragma unroll
-      for (int wd = 0; wd < NM; wd++) {
-        uint64_t x = mk[wd];
-        while (x) {
-          const int r = __ffsll((long long)x) - 1 + 64 * wd;
-          x &= x - 1;
-          s ^= sc.hs[r];
-        }
-      }
-      hit = s == 0;
-    }
+    const int lim = min(32, qlim - q);
+    if (lim <= 0) break;
+#ifdef SG_PHASE_PROFILE
+    nchunks++;
+#endif
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < lim) e = __ldg(O.ent + tb + q + lane);
+    const int w = e.x & 0xff;
+    const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
+    float l2sum;
+    const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr, l2sum) ^ h.s0;
+    const float mass = w > 0 ? exp2f(-l2sum) : 0.f;
+    const bool hit = lane < lim && s == 0;
     unsigned hm = __ballot_sync(FULL, hit);
     int stop_lane = -1;
     while (hm) {
       const int hl = __ffs(hm) - 1;
       hm &= hm - 1;
-      if (lane == hl) {
-        // record the list entry: codeword in bit order and log mass
-        uint64_t cw[NM];
-#pragma unroll
-        for (int wd = 0; wd < NM; wd++) cw[wd] = 0;
-        float ls = 0.f;
-#pragma unroll
-        for (int wd = 0; wd < NM; wd++) {
-          uint64_t x = mk[wd];
-          while (x) {
-            const int r = __ffsll((long long)x) - 1 + 64 * wd;
-            x &= x - 1;
-            ls += sc.al[r];
-            const int bi = sc.perm[r];
-#pragma unroll
-            for (int w2 = 0; w2 < NM; w2++)
-              if ((bi >> 6) == w2) cw[w2] ^= 1ull << (bi & 63);
-          }
-        }
-#pragma unroll
-        for (int wd = 0; wd < NM; wd++) {
-          uint64_t yw = 0;
-#pragma unroll
-          for (int hh = 0; hh < 2; hh++) {
-            const int kk = wd * 2 + hh;
-            if (kk < NPL) yw |= (uint64_t)h.yb[kk] << (32 * hh);
-          }
-          sc.cw[nhit * NM + wd] = cw[wd] ^ yw;
-          sc.zm[nhit * NM + wd] = mk[wd];
-        }
-        sc.lp[nhit] = -ls;
-      }
+      record_hit<NPL, SYN>(sc, h, e, hl, nhit, lane);
       nhit++;
       if (nhit >= P.L) {
         stop_lane = hl;
         break;
       }
       if (P.thr > 0.f) {
-        __syncwarp();
-        const int hC = __shfl_sync(FULL, lC, hl), hwi = __shfl_sync(FULL, lwi, hl), hpos = __shfl_sync(FULL, lpos, hl);
-        const float r2 = remaining_log2<NPL, SYN>(sc, W, n, cls, hC, hwi, hpos, lane, xf_count);
-        const float M = r2 * LN2_F + code.log_phi;
-        float D = M;
-        for (int l = 0; l < nhit; l++) D = lse(D, sc.lp[l]);
-        if (expf(M - D) < P.thr) {
+        const float tq = __shfl_sync(FULL, warp_sum_f(tmass + (lane <= hl ? mass : 0.f)), 0);
+        const float r2 = remaining_log2<NPL, SYN>(sc, O, tb, tc, q + hl, n, h.c, cls, lane, tq, xf_count);
+        if (thr_reached(sc, nhit, r2 * LN2_F + code.log_phi, P.thr)) {
           stop_lane = hl;
           lr2 = r2;
           have_lr2 = true;
@@ -784,28 +893,34 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
       }
     }
     if (stop_lane >= 0) {
+      if (lane <= stop_lane) {
+        wacc += w;
+        tmass += mass;
+      }
       q += stop_lane + 1;
-      sC = __shfl_sync(FULL, lC, stop_lane);
-      swi = __shfl_sync(FULL, lwi, stop_lane);
-      spos = __shfl_sync(FULL, lpos, stop_lane);
-      if (W.done && stop_lane == nv - 1) exhausted = true;
       break;
     }
-    q += nv;
-    if (q >= P.cap) {
-      sC = __shfl_sync(FULL, lC, nv - 1);
-      swi = __shfl_sync(FULL, lwi, nv - 1);
-      spos = __shfl_sync(FULL, lpos, nv - 1);
-      if (W.done) exhausted = true;
-      break;
-    }
+    wacc += w;  // lanes past lim hold an empty entry
+    tmass += mass;
+    q += lim;
   }
+  // the whole parity class has been queried: nothing remains
+  const bool exhausted = q >= tc && tc == O.class_size;
   __syncwarp();
+#ifdef SG_PHASE_PROFILE
+  const long long t2 = clock64();
+#endif
 
-  // soft output (Corollary + eq. LLRi), natural log domain
+  // soft output (Corollary + eq. LLRi)
   if (!have_lr2)
-    lr2 = exhausted ? -CUDART_INF_F : remaining_log2<NPL, SYN>(sc, W, n, cls, sC, swi, spos, lane, xf_count);
-  const float M = lr2 * LN2_F + code.log_phi;  // log (R phi)
+    lr2 = exhausted ? -CUDART_INF_F
+                    : remaining_log2<NPL, SYN>(sc, O, tb, tc, q - 1, n, h.c, cls, lane,
+                                               __shfl_sync(FULL, warp_sum_f(tmass), 0), xf_count);
+#ifdef SG_PHASE_PROFILE
+  const long long t3 = clock64();
+#endif
+  const float M = lr2 * LN2_F + code.log_phi;  // log (R phi), natural
+  res.wsum = (int32_t)__reduce_add_sync(FULL, (unsigned)wacc);
   res.queries = q;
   res.nhit = nhit;
   if (nhit == 0) {
@@ -813,27 +928,45 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     for (int k = 0; k < NPL; k++) lapp[k] = lam[k];
     res.pmiss = 1.f;
     res.logD = M;
-    return;
-  }
-  float D = M;
-  for (int l = 0; l < nhit; l++) D = lse(D, sc.lp[l]);
-  res.logD = D;
-  res.pmiss = M == -CUDART_INF_F ? 0.f : expf(M - D);
+  } else {
+    float D = M;
+    for (int l = 0; l < nhit; l++) D = lse(D, sc.lp[l]);
+    res.logD = D;
+    const float pm = M == -CUDART_INF_F ? 0.f : expf(M - D);
+    res.pmiss = pm;
+    // APP of each listed word (list weights relative to the normaliser)
+    if (lane < nhit) sc.wl[lane] = expf(sc.lp[lane] - D);
+    __syncwarp();
 #pragma unroll
-  for (int k = 0; k < NPL; k++) {
-    const int i = lane + 32 * k;
-    const float x = lam[k];
-    float a0 = M - softplus(-x);  // M + log sigma(x)
-    float a1 = M - softplus(x);   // M + log sigma(-x)
-    for (int l = 0; l < nhit; l++) {
-      const bool bit = (sc.cw[l * NM + (i >> 6)] >> (i & 63)) & 1ull;
-      if (bit)
-        a1 = lse(a1, sc.lp[l]);
-      else
-        a0 = lse(a0, sc.lp[l]);
+    for (int k = 0; k < NPL; k++) {
+      const int i = lane + 32 * k;
+      const float x = lam[k];
+      // sigma(x) and sigma(-x) without cancellation
+      const float ex = expf(-fabsf(x));
+      const float sp = 1.f / (1.f + ex), sn = ex * sp;  // sigma(|x|), sigma(-|x|)
+      float a0 = pm * (x >= 0.f ? sp : sn);              // miss term, bit 0
+      float a1 = pm * (x >= 0.f ? sn : sp);              // miss term, bit 1
+      const uint64_t bitm = 1ull << (i & 63);
+      for (int l = 0; l < nhit; l++) {
+        if (sc.cw[l * NM + (i >> 6)] & bitm)
+          a1 += sc.wl[l];
+        else
+          a0 += sc.wl[l];
+      }
+      lapp[k] = (a0 > 1e-30f && a1 > 1e-30f) ? logf(a0 / a1) : lapp_logdomain<NPL, SYN>(sc, nhit, M, x, i);
     }
-    lapp[k] = a0 - a1;
   }
+#ifdef SG_PHASE_PROFILE
+  const long long t4 = clock64();
+  if (lane == 0) {
+    SG_PROF(0, t1 - t0);
+    SG_PROF(1, t2 - t1);
+    SG_PROF(2, t3 - t2);
+    SG_PROF(3, t4 - t3);
+    SG_PROF(4, 1);
+    SG_PROF(5, nchunks);
+  }
+#endif
 }
 
 }  // namespace sg

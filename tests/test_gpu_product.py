@@ -44,7 +44,7 @@ def _decode(env, code, lch, **kw):
     c = sg.Code.from_linear_code(code)
     out = sg.product_decode(c, torch.from_numpy(np.ascontiguousarray(lch)).cuda(), **kw)
     torch.cuda.synchronize()
-    res = {k: v.cpu().numpy() for k, v in out.items()}
+    res = {k: v.cpu().numpy() for k, v in out.items() if hasattr(v, "cpu")}
     res["frames"] = sg.unpack_bits(out["bits"], code.n)
     c.close()
     return res

@@ -38,25 +38,33 @@ def _frames_in_block(code, nbits_info, nbits, rate, ebn0_db, seed, stream, b, lo
     return u, x, llr
 
 
-def _generate(code, count, ebn0_db, seed, stream, first, nbits_info, nbits, rate, encode):
+def _generate(code, count, ebn0_db, seed, stream, first, nbits_info, nbits, rate, encode, threads=None):
     ebn0 = np.broadcast_to(np.asarray(ebn0_db, dtype=np.float64), (count,))
-    U, X, LL = [], [], []
+    jobs = []
     f = first
     end = first + count
     while f < end:
         b = f // BLOCK
         lo = f - b * BLOCK
         hi = min(BLOCK, end - b * BLOCK)
-        u, x, llr = _frames_in_block(code, nbits_info, nbits, rate, ebn0[f - first:f - first + hi - lo],
-                                     seed, stream, b, lo, hi, encode)
-        U.append(u)
-        X.append(x)
-        LL.append(llr)
+        jobs.append((b, lo, hi, f - first))
         f += hi - lo
-    return np.concatenate(U), np.concatenate(X), np.concatenate(LL)
+
+    def run(job):
+        b, lo, hi, o = job
+        return _frames_in_block(code, nbits_info, nbits, rate, ebn0[o:o + hi - lo], seed, stream, b, lo, hi, encode)
+
+    if threads and threads > 1 and len(jobs) > 1:
+        from concurrent.futures import ThreadPoolExecutor
+        with ThreadPoolExecutor(threads) as ex:
+            parts = list(ex.map(run, jobs))
+    else:
+        parts = [run(j) for j in jobs]
+    return (np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts]),
+            np.concatenate([p[2] for p in parts]))
 
 
-def awgn_frames(code, count: int, ebn0_db, seed: int, first: int = 0, stream: int = 1):
+def awgn_frames(code, count: int, ebn0_db, seed: int, first: int = 0, stream: int = 1, threads: int | None = None):
     """Product-code frames: (U [F,k,k] u8, X [F,n,n] u8, L_Ch [F,n,n] f32).
 
     ``ebn0_db`` is a scalar or one value per frame; the rate is the product
@@ -64,11 +72,11 @@ def awgn_frames(code, count: int, ebn0_db, seed: int, first: int = 0, stream: in
     """
     n, k = code.n, code.k
     U, X, L = _generate(code, count, ebn0_db, seed, stream, first, k * k, n * n, (k * k) / (n * n),
-                        lambda u: code.product_encode(u.reshape(-1, k, k)))
+                        lambda u: code.product_encode(u.reshape(-1, k, k)), threads)
     return U.reshape(-1, k, k), X.reshape(-1, n, n), L.reshape(-1, n, n)
 
 
-def awgn_words(code, count: int, ebn0_db, seed: int, first: int = 0, stream: int = 2):
+def awgn_words(code, count: int, ebn0_db, seed: int, first: int = 0, stream: int = 2, threads: int | None = None):
     """Independent component words: (U [W,k], X [W,n], L_Ch [W,n] f32) at the component rate."""
     return _generate(code, count, ebn0_db, seed, stream, first, code.k, code.n, code.k / code.n,
-                     lambda u: code.encode(u))
+                     lambda u: code.encode(u), threads)
