@@ -180,6 +180,44 @@ int product_decode_host(sogrand_code *row_code, const sogrand_code *col_code, in
                         const float *llr_ch, int L, int64_t query_cap, float thr, float alpha, int max_iter,
                         uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries, void *stream);
 
+/* Size of the fixed device array behind product_decode_noalloc. */
+#define SOGRAND_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+/*
+ * product_decode for callers that cannot allocate device memory.  The paper
+ * has no counterpart: this is a deployment variant.  Some callers may not
+ * call cudaMalloc or a stream-ordered allocator: code that runs with a
+ * fixed, pre-reserved memory budget (a real-time receiver pipeline, an
+ * embedded deployment), or code that must not add allocations, and with them
+ * implicit synchronisation, to a stream other work depends on.
+ * product_decode_noalloc takes its scratch (extrinsic state, hard decisions,
+ * frame flags, about 4 n^2 + 8 n ceil(n/64) + 16 bytes per frame) from one
+ * fixed device array of SOGRAND_NOALLOC_SCRATCH_BYTES, which every GPU that
+ * loads the library holds until the process exits.  The call allocates
+ * nothing: no cudaMalloc, cudaFree or allocating library routine.
+ *   arguments and results as for product_decode, except that half_iters,
+ *   status and queries are required; every output is device memory.
+ *   The call is asynchronous on `stream` and always launches all 2 *
+ *   max_iter half iterations (frames that finished are skipped).
+ *   The first call on a device looks up the array's device address on that
+ *   device (cudaGetSymbolAddress); make that first call before any stream
+ *   capture.  The query-order tables of the code must already cover
+ *   query_cap (sogrand_code_create covers 10^4; larger caps need
+ *   sogrand_code_reserve first), because growing them allocates.
+ *   All calls share the array and it keeps the last call's contents; every
+ *   call clears what must start at zero.  Calls that overlap on the GPU (on
+ *   different streams, or from different threads) race on the array and
+ *   produce wrong results; serialise them.
+ * Errors: EINVAL also when n_frames needs more scratch than the array holds
+ * (the bound is 4 n^2 F + 8 n ceil(n/64) F + 16 F bytes plus up to 1280
+ * bytes of alignment, within SOGRAND_NOALLOC_SCRATCH_BYTES; for n = 64 about
+ * 1980 frames) or when the tables do not cover query_cap; EUNSUPPORTED,
+ * ECUDA as for product_decode.  Nothing is written on an argument error.
+ */
+int product_decode_noalloc(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames,
+                           const float *llr_ch, int L, int64_t query_cap, float thr, float alpha, int max_iter,
+                           uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries, void *stream);
+
 /*
  * Test hook: the device's canonical query order for one word.
  *   llr          HOST [n] lambda values

@@ -582,6 +582,101 @@ int sogrand_trace_patterns(sogrand_code *c, const float *llr, int64_t max_q, uin
   return SOGRAND_OK;
 }
 
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// product_decode_noalloc: product decoding for callers that may not allocate
+// ---------------------------------------------------------------------------
+// The scratch of the turbo decoder (extrinsic state, hard decisions, frame
+// flags) lives in this fixed device array instead of stream-ordered
+// allocations.  Every GPU that loads the library holds it until the process
+// exits.  Host code only sees a stand-in for the array's name, so its device
+// address is taken once per device with cudaGetSymbolAddress and passed to
+// the kernels as a plain pointer.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[SOGRAND_NOALLOC_SCRATCH_BYTES];
+
+namespace {
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {nullptr};
+}  // namespace
+
+extern "C" {
+
+int product_decode_noalloc(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
+                           int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                           uint8_t *status, int64_t *queries, void *stream) {
+  if (!rc_ || !cc_ || F < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f) ||
+      !(alpha > 0.f && alpha < 1e6f) || max_iter < 1 || max_iter > 1000)
+    return SOGRAND_EINVAL;
+  if (rc_ != cc_) return SOGRAND_EUNSUPPORTED;
+  sogrand_code *c = rc_;
+  if (c->n - 1 < 63 && cap >= (int64_t(1) << (c->n - 1))) return SOGRAND_EINVAL;
+  if (F == 0) return SOGRAND_OK;
+  if (!llr_ch || !bits || !half_iters || !status || !queries) return SOGRAND_EINVAL;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SOGRAND_ECUDA;
+  if (dev != c->device || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return SOGRAND_EINVAL;
+  {
+    // the query-order tables must already cover the cap: growing them allocates
+    std::lock_guard<std::mutex> g(c->mu);
+    if (cap > c->tab_cap) return SOGRAND_EINVAL;
+  }
+  const int n = c->n, nm = c->nm;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_le = (size_t)F * n * n * sizeof(float), b_hb = (size_t)F * n * nm * sizeof(uint64_t);
+  const size_t b_i32 = (size_t)F * sizeof(int32_t), b_i64 = (size_t)F * sizeof(int64_t);
+  const size_t need = al(b_le) + al(b_hb) + 2 * al(b_i32) + al(b_i64);
+  if (need > (size_t)SOGRAND_NOALLOC_SCRATCH_BYTES) return SOGRAND_EINVAL;  // too many frames for the fixed scratch
+  void *base = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+      // device address of the array on the current device (set-up, once per device)
+      if (cudaGetSymbolAddress(&g_noalloc_ptr[dev], g_noalloc_scratch) != cudaSuccess) {
+        g_noalloc_ptr[dev] = nullptr;
+        return SOGRAND_ECUDA;
+      }
+    }
+    base = g_noalloc_ptr[dev];
+  }
+  char *p = (char *)base;
+  auto take = [&p, &al](size_t bytes) {
+    char *r = p;
+    p += al(bytes);
+    return r;
+  };
+  cudaStream_t s = (cudaStream_t)stream;
+  sg::ProductArgs a{};
+  a.n_frames = F;
+  a.llr_ch = llr_ch;
+  a.alpha = alpha;
+  a.max_half = 2 * max_iter;
+  a.le = (float *)take(b_le);
+  a.hb = (uint64_t *)take(b_hb);
+  a.fstate = (int32_t *)take(b_i32);
+  a.hmax = (int32_t *)take(b_i32);
+  a.par_queries = (int64_t *)take(b_i64);
+  a.active = nullptr;
+  a.bits = bits;
+  a.half_iters = half_iters;
+  a.status = status;
+  a.queries = queries;
+  sg::DevCode d = dev_code(c);
+  sg::SisoParams P{L, (int32_t)cap, thr};
+  // frame flags, per-half maxima and counters start at zero on every call
+  // (the array keeps the previous call's contents)
+  cudaError_t e = cudaSuccess;
+  SG_DISPATCH(c, e = (sg::launch_product_init<NPL, SYN>(d, a, s)));
+  // every half iteration is launched; the kernels skip frames that finished,
+  // so the host never waits on the device
+  for (int h = 1; h <= a.max_half && e == cudaSuccess; h++) {
+    SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, P, a, h, s)));
+    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, a, h, s)));
+  }
+  return e == cudaSuccess ? SOGRAND_OK : SOGRAND_ECUDA;
+}
+
 #ifdef SG_PHASE_PROFILE
 // phase counters of the profiling build (not part of the public ABI)
 int sogrand_debug_phase(unsigned long long *out, int reset) {
