@@ -142,6 +142,9 @@ def main():
     ap.add_argument("--ref-frames", type=int, default=28, help="oracle sample per reference step")
     ap.add_argument("--cpu-frames", type=int, default=112, help="oracle sample for cpu_baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--form", default="persistent", choices=["persistent", "plain"],
+                    help="persistent: one kernel per decode with a device-side frame queue; plain: one launch per half")
+    ap.add_argument("--plain-steps", type=int, default=3, help="steps of the other form, timed for comparison (0: off)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -181,44 +184,56 @@ def main():
                weight_sum=torch.zeros(1, dtype=torch.int64, device=dev),
                xf_words=torch.zeros(1, dtype=torch.int32, device=dev))
 
-    def step():
-        return sg.product_decode(c, d_in, L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER, out=out)
+    def step(persistent):
+        return sg.product_decode(c, d_in, L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER, out=out,
+                                 persistent=persistent)
 
-    for i in range(args.warmup):
-        t0 = time.perf_counter()
-        step()
+    def timed(persistent, steps, warmup, sample_clocks):
+        for i in range(warmup):
+            t0 = time.perf_counter()
+            step(persistent)
+            torch.cuda.synchronize()
+            log(f"{'persistent' if persistent else 'plain'} warm-up step {i}: {1000 * (time.perf_counter() - t0):.1f} ms")
+        out["weight_sum"].zero_()
+        clocks = ClockSampler() if sample_clocks else None
+        if dist:
+            dist.barrier()
         torch.cuda.synchronize()
-        log(f"warm-up step {i}: {1000 * (time.perf_counter() - t0):.1f} ms")
-    out["weight_sum"].zero_()
-    clocks = ClockSampler()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    stream = torch.cuda.current_stream()
-    ev0.record(stream)
-    t_half = t_check = 0.0
-    launches = half_launches = 0
-    qtot = 0
-    for _ in range(args.steps):
-        o = step()
-        t_half += o["timing_ms"][0]
-        t_check += o["timing_ms"][1]
-        launches += o["launches"]
-        half_launches += o["launches"] // 2
-        qtot += int(out["queries"].sum().item())
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    clk = clocks.stop()
-    ms = ev0.elapsed_time(ev1)
-    log(f"timed: {args.steps} steps in {ms:.1f} ms")
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    wsum = int(out["weight_sum"].item())
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        stream = torch.cuda.current_stream()
+        ev0.record(stream)
+        t_kern = t_check = 0.0
+        launches = kern_launches = 0
+        qtot = 0
+        for _ in range(steps):
+            o = step(persistent)
+            t_kern += o["timing_ms"][0]
+            t_check += o["timing_ms"][1]
+            launches += o["launches"]
+            kern_launches += 1 if persistent else o["launches"] // 2
+            qtot += int(out["queries"].sum().item())
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        clk = clocks.stop() if clocks else None
+        ms = ev0.elapsed_time(ev1)
+        log(f"{'persistent' if persistent else 'plain'} timed: {steps} steps in {ms:.1f} ms")
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return dict(ms=ms, t_kern=t_kern, t_check=t_check, launches=launches, kern_launches=kern_launches, qtot=qtot,
+                    clk=clk, wsum=int(out["weight_sum"].item()))
+
+    main_persistent = args.form == "persistent"
+    other = None
+    if args.plain_steps > 0:
+        other = timed(not main_persistent, args.plain_steps, 1, False)
+    r = timed(main_persistent, args.steps, args.warmup, True)
+    ms, t_half, t_check, launches, half_launches, qtot, clk = (r["ms"], r["t_kern"], r["t_check"], r["launches"],
+                                                                r["kern_launches"], r["qtot"], r["clk"])
+    wsum = r["wsum"]
     info_bits = world * F * k * k * args.steps
     value = info_bits / (ms / 1000)
 
@@ -229,7 +244,7 @@ def main():
     achieved = ops / (t_half / 1000) / 1e12 if t_half > 0 else 0.0
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak if peak else None, "traffic": None,
-                "kernel": "k_product_half", "launches": half_launches,
+                "kernel": "k_product_persistent" if main_persistent else "k_product_half", "launches": half_launches,
                 "avg_launch_ms": t_half / max(half_launches, 1),
                 "ops_per_launch": ops / max(half_launches, 1),
                 "ops_def": "2 x (queries + summed pattern weights)",
@@ -285,7 +300,14 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(F),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "queries_per_s": world * qtot / (ms / 1000), "xf_words": int(out["xf_words"].item()),
-                "quality": quality, "form": "plain (one launch per half iteration)"}
+                "quality": quality,
+                "form": ("persistent (one kernel per decode, device-side frame queue)" if main_persistent
+                         else "plain (one launch per half iteration)")}
+        if other is not None:
+            line["other_form"] = {"form": "plain" if main_persistent else "persistent",
+                                  "value": world * F * k * k * args.plain_steps / (other["ms"] / 1000),
+                                  "ms_per_step": other["ms"] / args.plain_steps, "steps": args.plain_steps,
+                                  "gpu_launches": other["launches"]}
         print(json.dumps(line), flush=True)
     c.close()
     if dist:

@@ -167,14 +167,37 @@ int product_decode_ex(sogrand_code *row_code, const sogrand_code *col_code, int6
                       void *stream);
 
 /*
- * product_decode on HOST buffers: copies llr_ch to the device, decodes and
- * copies the results back before returning (device buffers are allocated
+ * Batched form of product_decode_ex: the whole batch is decoded by one
+ * persistent kernel (Sec. VI decoding, same arithmetic, same results as
+ * product_decode_ex).  Frames wait in a device-side queue; warps take word
+ * tickets from the frame at its head, and the warp that completes a frame's
+ * last word of a half runs that frame's row/column check and either finishes
+ * the frame or queues it for its next half.  No per-half launches and no
+ * host round trips; every frame advances at its own pace.  Waits inside the
+ * kernel are bounded: if the queue stays empty for about 2^22 polls while
+ * frames are unfinished the kernel stops and the call returns
+ * SOGRAND_ETIMEOUT.  stats->timing_ms[0] is the kernel's device time;
+ * launches counts 2 (queue set-up and the decoder).  Scratch, allocated
+ * stream-ordered: about 4 n^2 + 8 n ceil(n/64) + 36 bytes per frame.  The
+ * call synchronises `stream` at its end to read the kernel's status.
+ * Errors: as product_decode_ex, plus ETIMEOUT; EINVAL also if
+ * n_frames * 2 * max_iter >= 2^31.
+ */
+int product_decode_persistent(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames,
+                              const float *llr_ch, int L, int64_t query_cap, float thr, float alpha, int max_iter,
+                              uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
+                              product_decode_stats *stats, void *stream);
+
+/*
+ * product_decode on HOST buffers: copies llr_ch to the device, decodes with
+ * the batched form (product_decode_persistent) and copies the results back
+ * before returning (device buffers are allocated
  * stream-ordered on `stream` and freed before return).  Pinned host memory
  * makes the copies asynchronous DMA; pageable memory works too.
  *   llr_ch     HOST [n_frames][n][n]
  *   bits       HOST [n_frames][ceil(n*n/8)] (required)
  *   half_iters, status, queries  HOST [n_frames] (each may be NULL)
- * Errors: as product_decode.
+ * Errors: as product_decode_persistent.
  */
 int product_decode_host(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames,
                         const float *llr_ch, int L, int64_t query_cap, float thr, float alpha, int max_iter,

@@ -55,11 +55,14 @@ def load() -> C.CDLL:
         L.product_decode_ex.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp,
                                         C.POINTER(ProductStats), vp]
         L.product_decode_host.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp]
+        L.product_decode_persistent.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp,
+                                                C.POINTER(ProductStats), vp]
         L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
-                     "product_decode", "product_decode_ex", "product_decode_host", "sogrand_trace_patterns"):
+                     "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
+                     "sogrand_trace_patterns"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -157,9 +160,12 @@ def sogrand_decode(code: Code, llr_ch, llr_a=None, L: int = 4, query_cap: int = 
 
 
 def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
-                   max_iter: int = 20, col_code: Code | None = None, stream=None, out=None, stats: bool = True) -> dict:
+                   max_iter: int = 20, col_code: Code | None = None, stream=None, out=None, stats: bool = True,
+                   persistent: bool = False) -> dict:
     """Decode [F, n, n] frames (float32 CUDA tensor); returns CUDA tensors (and,
-    with stats, host-side timing_ms / launches)."""
+    with stats, host-side timing_ms / launches).  persistent=True uses the
+    batched form (product_decode_persistent), else one launch per half
+    (product_decode_ex)."""
     import torch
     F, n, n2 = llr_ch.shape
     assert n == n2 == code.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
@@ -179,11 +185,11 @@ def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: 
         ln = (C.c_int32 * 1)()
         st = ProductStats(_ptr(out.get("par_queries")), _ptr(out.get("weight_sum")), _ptr(out.get("xf_words")),
                           C.cast(tm, C.POINTER(C.c_float)), C.cast(ln, C.POINTER(C.c_int32)))
-    rc = load().product_decode_ex(code.handle, cc.handle, F, _ptr(llr_ch), int(L), int(query_cap), float(thr),
-                                  float(alpha), int(max_iter), _ptr(out["bits"]), _ptr(out.get("half_iters")),
-                                  _ptr(out.get("status")), _ptr(out.get("queries")),
-                                  C.byref(st) if st is not None else None, _stream(stream))
-    _check(rc, "product_decode")
+    fn = load().product_decode_persistent if persistent else load().product_decode_ex
+    rc = fn(code.handle, cc.handle, F, _ptr(llr_ch), int(L), int(query_cap), float(thr), float(alpha), int(max_iter),
+            _ptr(out["bits"]), _ptr(out.get("half_iters")), _ptr(out.get("status")), _ptr(out.get("queries")),
+            C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "product_decode_persistent" if persistent else "product_decode")
     if stats:
         out["timing_ms"] = (float(tm[0]), float(tm[1]))
         out["launches"] = int(ln[0])

@@ -507,6 +507,88 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   return SOGRAND_OK;
 }
 
+int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
+                              int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                              uint8_t *status, int64_t *queries, product_decode_stats *stats, void *stream) {
+  int64_t *par_queries = stats ? stats->par_queries : nullptr;
+  if (stats && stats->timing_ms) stats->timing_ms[0] = stats->timing_ms[1] = 0.f;
+  if (stats && stats->launches) stats->launches[0] = 0;
+  if (!rc_ || !cc_ || F < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f) ||
+      !(alpha > 0.f && alpha < 1e6f) || max_iter < 1 || max_iter > 1000)
+    return SOGRAND_EINVAL;
+  if (rc_ != cc_) return SOGRAND_EUNSUPPORTED;
+  sogrand_code *c = rc_;
+  if (c->n - 1 < 63 && cap >= (int64_t(1) << (c->n - 1))) return SOGRAND_EINVAL;
+  if (F == 0) return SOGRAND_OK;
+  if (!llr_ch || !bits) return SOGRAND_EINVAL;
+  // word tickets (slots x n, plus one per idle warp) are 32-bit
+  if (F * 2 * (int64_t)max_iter * rc_->n >= (int64_t(1) << 31) - (int64_t(1) << 22)) return SOGRAND_EINVAL;
+  int rc = ensure_cap(c, cap);
+  if (rc != SOGRAND_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = c->n, nm = c->nm;
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t b_le = (size_t)F * n * n * sizeof(float), b_hb = (size_t)F * n * nm * sizeof(uint64_t);
+  const size_t b_i32 = (size_t)F * sizeof(int32_t), b_i64 = (size_t)F * sizeof(int64_t);
+  const size_t b_queue = (size_t)F * 2 * max_iter * sizeof(int32_t);
+  const size_t total = al(b_le) + al(b_hb) + 4 * al(b_i32) + al(b_queue) + (half_iters ? 0 : al(b_i32)) +
+                       (queries ? 0 : al(b_i64)) + (par_queries ? 0 : al(b_i64)) + (status ? 0 : al((size_t)F)) +
+                       al(4 * sizeof(int32_t));
+  char *mem = nullptr;
+  if (cudaMallocAsync((void **)&mem, total, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  char *p = mem;
+  auto take = [&p, &al](size_t bytes) {
+    char *r = p;
+    p += al(bytes);
+    return r;
+  };
+  sg::ProductArgs a{};
+  a.n_frames = F;
+  a.llr_ch = llr_ch;
+  a.alpha = alpha;
+  a.max_half = 2 * max_iter;
+  a.le = (float *)take(b_le);
+  a.hb = (uint64_t *)take(b_hb);
+  a.hmax = (int32_t *)take(b_i32);
+  a.half_cur = (int32_t *)take(b_i32);
+  a.done_words = (int32_t *)take(b_i32);
+  a.bad = (int32_t *)take(b_i32);
+  a.queue = (int32_t *)take(b_queue);
+  a.bits = bits;
+  a.half_iters = half_iters ? half_iters : (int32_t *)take(b_i32);
+  a.queries = queries ? queries : (int64_t *)take(b_i64);
+  a.par_queries = par_queries ? par_queries : (int64_t *)take(b_i64);
+  a.status = status ? status : (uint8_t *)take((size_t)F);
+  a.ctrl = (int32_t *)take(4 * sizeof(int32_t));
+  a.max_spin = 2000000;  // 2 s of back-off without any work
+  a.xf_count = stats ? stats->xf_words : nullptr;
+  a.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
+  sg::DevCode d = dev_code(c);
+  sg::SisoParams P{L, (int32_t)cap, thr};
+  const bool timed = stats && stats->timing_ms;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaSuccess;
+  if (timed)
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, P, a, s)));
+  if (e == cudaSuccess && timed) e = cudaEventRecord(ev[1], s);
+  int32_t err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, a.ctrl + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && timed) {
+    float x = 0.f;
+    e = cudaEventElapsedTime(&x, ev[0], ev[1]);
+    stats->timing_ms[0] = x;
+  }
+  for (int i = 0; i < 2; i++)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (stats && stats->launches) stats->launches[0] = 2;  // queue set-up + the persistent kernel
+  cudaError_t e2 = cudaFreeAsync(mem, s);
+  if (e != cudaSuccess || e2 != cudaSuccess) return SOGRAND_ECUDA;
+  return err ? SOGRAND_ETIMEOUT : SOGRAND_OK;
+}
+
 int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
                         int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
                         uint8_t *status, int64_t *queries, void *stream) {
@@ -528,7 +610,8 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   int rc = SOGRAND_OK;
   if (cudaMemcpyAsync(d_in, llr_ch, b_in, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = SOGRAND_ECUDA;
   if (rc == SOGRAND_OK)
-    rc = product_decode_ex(rc_, cc_, F, d_in, L, cap, thr, alpha, max_iter, d_bits, d_hi, d_st, d_q, nullptr, stream);
+    rc = product_decode_persistent(rc_, cc_, F, d_in, L, cap, thr, alpha, max_iter, d_bits, d_hi, d_st, d_q, nullptr,
+                                   stream);
   if (rc == SOGRAND_OK) {
     cudaError_t e = cudaMemcpyAsync(bits, d_bits, b_bits, cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess && half_iters) e = cudaMemcpyAsync(half_iters, d_hi, (size_t)F * 4, cudaMemcpyDeviceToHost, s);

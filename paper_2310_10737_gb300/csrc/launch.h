@@ -44,6 +44,13 @@ struct ProductArgs {
   int32_t *active;       // [1] frames still running after the last check (scratch, may be null)
   int32_t *xf_count;
   unsigned long long *wsum;  // [1] += summed pattern weights of all queries (may be null)
+  // persistent form only (scratch)
+  int32_t *queue;             // [F * max_half] frame-halves: frame + 1 once a slot is filled, else 0
+  int32_t *half_cur;          // [F] current half iteration of each frame
+  int32_t *done_words;        // [F] words of the current half completed
+  int32_t *bad;               // [F] a non-finite input was seen
+  int32_t *ctrl;              // [4] slots reserved, word tickets, finished frames, error
+  int32_t max_spin;           // microseconds of accumulated back-off without work before giving up
 };
 
 template <int NPL, class SYN>
@@ -62,6 +69,9 @@ cudaError_t launch_product_half(const DevCode &code, const SisoParams &P, const 
 
 template <int NPL, class SYN>
 cudaError_t launch_product_check(const DevCode &code, const ProductArgs &a, int half, cudaStream_t s);
+
+template <int NPL, class SYN>
+cudaError_t launch_product_persistent(const DevCode &code, const SisoParams &P, const ProductArgs &a, cudaStream_t s);
 
 int scratch_bytes(int npl, int syn_bytes, int jmax);
 

@@ -142,3 +142,29 @@ def test_product_edge_cases(env, oracle_lib):
     with pytest.raises(sg.SograndError):
         sg.product_decode(c, torch.from_numpy(lch).cuda(), query_cap=2 ** 15)  # whole parity class
     c.close()
+
+
+@pytest.mark.parametrize("name,ebn0,F,max_iter", [("ebch_16_11", 2.0, 37, 10), ("ebch_32_26", 2.75, 300, 4),
+                                                  ("ebch_64_57", 2.75, 200, 20), ("ebch_64_51", 3.0, 50, 8),
+                                                  ("ebch_128_120", 3.75, 24, 5), ("ebch_32_26", 3.0, 3, 2)])
+def test_persistent_form_equals_plain_form(env, name, ebn0, F, max_iter):
+    """The batched form (one persistent kernel, device-side frame queue) runs
+    the same arithmetic per frame and half as the plain form, so every output
+    is identical."""
+    torch, sg = env
+    code = ebch(name)
+    U, X, lch = awgn_frames(code, F, ebn0, seed=600 + F)
+    if F > 10:
+        lch[F // 2, 1, 2] = np.nan  # one frame with a non-finite input
+    c = sg.Code.from_linear_code(code)
+    d = torch.from_numpy(lch).cuda()
+    outs = []
+    for persistent in (False, True):
+        o = sg.product_decode(c, d, L=4, query_cap=10**4, alpha=0.5, max_iter=max_iter, persistent=persistent)
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy() for k, v in o.items() if hasattr(v, "cpu")})
+    c.close()
+    for key in ("bits", "half_iters", "status", "queries", "par_queries", "weight_sum"):
+        np.testing.assert_array_equal(outs[1][key], outs[0][key], err_msg=key)
+    if F > 10:
+        assert outs[1]["status"][F // 2] == 2
