@@ -94,6 +94,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows), "power_w_max": max(pw) if pw else None}
 
 
+def rank_seed(rank):
+    """Each rank decodes its own seeded batch (weak scaling: frames are independent)."""
+    return SEED + rank
+
+
+def max_over_ranks(x, dist, dev):
+    """The slowest rank's figure (the timed region ends when every rank is done)."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, frames, info_bits_per_frame, steps, ms):
+    """Whole-job information bits/s: every rank's frames over the slowest rank's time."""
+    return world * frames * info_bits_per_frame * steps / (ms / 1000)
+
+
 def cpu_oracle_rate(code, lch, threads):
     """The oracle (FP64, plain C, all host cores) on a bounded sample: info bits/s."""
     import oracle
@@ -139,8 +159,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per rank per step (default: the workload)")
-    ap.add_argument("--ref-frames", type=int, default=28, help="oracle sample per reference step")
-    ap.add_argument("--cpu-frames", type=int, default=112, help="oracle sample for cpu_baseline")
+    ap.add_argument("--ref-frames", type=int, default=700, help="oracle sample per reference step")
+    ap.add_argument("--cpu-frames", type=int, default=3500, help="oracle sample for cpu_baseline")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--form", default="persistent", choices=["persistent", "plain"],
                     help="persistent: one kernel per decode with a device-side frame queue; plain: one launch per half")
@@ -169,7 +189,7 @@ def main():
     F = args.frames
     cores = os.cpu_count() or 1
     t0 = time.perf_counter()
-    U, X, lch = make_inputs(code, F, SEED + rank, cores)
+    U, X, lch = make_inputs(code, F, rank_seed(rank), cores)
     log(f"inputs: {F} frames in {time.perf_counter() - t0:.1f} s")
     host = torch.from_numpy(lch).pin_memory()
     d_in = host.to(dev)
@@ -219,10 +239,7 @@ def main():
         clk = clocks.stop() if clocks else None
         ms = ev0.elapsed_time(ev1)
         log(f"{'persistent' if persistent else 'plain'} timed: {steps} steps in {ms:.1f} ms")
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, dist, dev)
         return dict(ms=ms, t_kern=t_kern, t_check=t_check, launches=launches, kern_launches=kern_launches, qtot=qtot,
                     clk=clk, wsum=int(out["weight_sum"].item()))
 
@@ -234,8 +251,7 @@ def main():
     ms, t_half, t_check, launches, half_launches, qtot, clk = (r["ms"], r["t_kern"], r["t_check"], r["launches"],
                                                                 r["kern_launches"], r["qtot"], r["clk"])
     wsum = r["wsum"]
-    info_bits = world * F * k * k * args.steps
-    value = info_bits / (ms / 1000)
+    value = job_rate(world, F, k * k, args.steps, ms)
 
     # roofline of the dominant kernel (the half-iteration SISO kernel): integer ALU
     ops = 2 * (qtot + wsum)  # per query: w syndrome XORs + 1 membership test, and w + 1 mass terms (Sec. IV)
@@ -265,11 +281,8 @@ def main():
         e2e_ms.append(1000 * (time.perf_counter() - t))
     e2e_t = min(e2e_ms)
     log(f"end to end: {e2e_ms}")
-    if dist:
-        t = torch.tensor([e2e_t], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_t = float(t.item())
-    e2e = {"value": world * F * k * k / (e2e_t / 1000), "unit": "bits/s",
+    e2e_t = max_over_ranks(e2e_t, dist, dev)
+    e2e = {"value": job_rate(world, F, k * k, 1, e2e_t), "unit": "bits/s",
            "h2d_bytes_per_step": int(F * n * n * 4), "d2h_bytes_per_step": int(F * (n * n // 8 + 4 + 1 + 8)),
            "api": "product_decode_host (C ABI, pinned host buffers)"}
 
@@ -292,7 +305,8 @@ def main():
         rate, dt = cpu_oracle_rate(code, lch[: args.cpu_frames], cores)
         log(f"cpu baseline: {args.cpu_frames} frames in {dt:.1f} s")
         cpu = {"value": rate, "unit": "bits/s", "cores": cores, "kind": "oracle",
-               "sample": f"first {args.cpu_frames} frames of the workload (16 per Eb/N0 point), {dt:.1f} s wall"}
+               "sample": f"first {args.cpu_frames} frames of the workload ({args.cpu_frames // 7} per Eb/N0 point), "
+                         f"{dt:.1f} s wall"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "bits/s", "n_gpus": world, "steps": args.steps,
@@ -305,7 +319,7 @@ def main():
                          else "plain (one launch per half iteration)")}
         if other is not None:
             line["other_form"] = {"form": "plain" if main_persistent else "persistent",
-                                  "value": world * F * k * k * args.plain_steps / (other["ms"] / 1000),
+                                  "value": job_rate(world, F, k * k, args.plain_steps, other["ms"]),
                                   "ms_per_step": other["ms"] / args.plain_steps, "steps": args.plain_steps,
                                   "gpu_launches": other["launches"]}
         print(json.dumps(line), flush=True)

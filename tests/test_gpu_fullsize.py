@@ -1,0 +1,124 @@
+"""GPU parity at the benchmark configurations' full sizes.
+
+* eBCH(32,26)^2, 200 frames at 3.0 dB, L = 4, cap 10^4, 4 iterations (the
+  plain-method configuration), both product forms against the oracle;
+* component-only SISO: 10^6 eBCH(64,57) words and 10^6 eBCH(32,26) words over
+  2/3/4/5 dB, L in {1, 2, 4}, query cap 10^5, in one launch per code and L; a
+  random sample of words is compared with the oracle word by word;
+* eBCH(64,57)^2, 100,000 frames over 2.5..4.0 dB (the benchmarked batch and
+  launch configuration): a sample of frames against the oracle, and on every
+  frame the properties that hold at any size (success iff every row and column
+  is a codeword, half-iteration bounds, query-count consistency).
+"""
+import numpy as np
+import pytest
+
+from gpu_common import compare_siso
+from workloads import awgn_frames, awgn_words, ebch
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env(oracle_lib):
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_10737_gb300 as sg
+    return torch, sg
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_plain_method_configuration(env, oracle_lib, persistent):
+    torch, sg = env
+    code = ebch("ebch_32_26")
+    U, X, lch = awgn_frames(code, 200, 3.0, seed=1)
+    c = sg.Code.from_linear_code(code)
+    o = sg.product_decode(c, torch.from_numpy(lch).cuda(), L=4, query_cap=10**4, alpha=0.5, max_iter=4,
+                          persistent=persistent)
+    torch.cuda.synchronize()
+    g = sg.unpack_bits(o["bits"], code.n)
+    hi = o["half_iters"].cpu().numpy()
+    q = o["queries"].cpu().numpy()
+    c.close()
+    r = oracle_lib.product_batch(oracle_lib.OracleCode(code), lch, L=4, cap=10**4, alpha=0.5, max_iter=4)
+    first = r["half_iters"] == 1
+    np.testing.assert_array_equal(hi[first], 1)
+    np.testing.assert_array_equal(q[first], r["queries"][first])
+    np.testing.assert_array_equal(g[first], r["bits"][first])
+    same = (g == r["bits"]).reshape(200, -1).all(axis=1)
+    assert same.mean() >= 0.99
+    err_g = (g != X).reshape(200, -1).any(axis=1).sum()
+    err_o = (r["bits"] != X).reshape(200, -1).any(axis=1).sum()
+    assert abs(int(err_g) - int(err_o)) <= max(2, 0.2 * err_o)
+
+
+@pytest.mark.parametrize("name", ["ebch_64_57", "ebch_32_26"])
+def test_component_siso_configuration_full_size(env, oracle_lib, name):
+    torch, sg = env
+    code = ebch(name)
+    W = 10**6
+    snr = np.array([2.0, 3.0, 4.0, 5.0])[np.arange(W) % 4]
+    _, _, lch = awgn_words(code, W, snr, seed=2, threads=16)
+    c = sg.Code.from_linear_code(code)
+    c.reserve(10**5)
+    d = torch.from_numpy(lch).cuda()
+    rng = np.random.default_rng(3)
+    sample = np.sort(rng.choice(W, 96, replace=False))
+    oc = oracle_lib.OracleCode(code)
+    for L in (1, 2, 4):
+        out = sg.sogrand_decode(c, d, L=L, query_cap=10**5)
+        torch.cuda.synchronize()
+        q = out["queries"].cpu().numpy()
+        assert (q >= 1).all() and (q <= 10**5).all()
+        sub = {k: v[torch.from_numpy(sample).cuda()] for k, v in out.items()}
+        ref = oracle_lib.siso_batch(oc, lch[sample], L=L, cap=10**5)
+        compare_siso(code, sub, ref, f"{name} full size L={L}")
+    c.close()
+
+
+def test_benchmark_batch_full_size(env, oracle_lib):
+    torch, sg = env
+    code = ebch("ebch_64_57")
+    n, k = code.n, code.k
+    F = 100_000
+    snr = (2.5 + 0.25 * np.arange(7))[np.arange(F) % 7]
+    U, X, lch = awgn_frames(code, F, snr, seed=2310, threads=16)
+    c = sg.Code.from_linear_code(code)
+    o = sg.product_decode(c, torch.from_numpy(lch).cuda(), L=4, query_cap=10**4, alpha=0.5, max_iter=20,
+                          persistent=True)
+    torch.cuda.synchronize()
+    status = o["status"].cpu().numpy()
+    hi = o["half_iters"].cpu().numpy()
+    q = o["queries"].cpu().numpy()
+    pq = o["par_queries"].cpu().numpy()
+    bits = o["bits"].cpu().numpy()
+    c.close()
+    assert ((hi >= 1) & (hi <= 40)).all()
+    assert (status <= 1).all()
+    assert (hi[status == 1] == 40).all()
+    assert (pq <= q).all() and (pq * n >= q).all() and (q >= hi).all()
+    # success iff every row and column is a codeword (independent syndrome check)
+    for lo in range(0, F, 10_000):
+        B = sg.unpack_bits(bits[lo:lo + 10_000], n).astype(np.float32)
+        Ht = code.H.T.astype(np.float32)
+        rows_ok = ~((B @ Ht).astype(np.int64) & 1).any(axis=(1, 2))
+        cols_ok = ~((B.transpose(0, 2, 1) @ Ht).astype(np.int64) & 1).any(axis=(1, 2))
+        np.testing.assert_array_equal(rows_ok & cols_ok, status[lo:lo + 10_000] == 0)
+    # a sample of frames, four per Eb/N0 point, against the oracle
+    sample = np.concatenate([np.arange(i, F, 7)[[0, 1, 1000, 9000]] for i in range(7)])
+    r = oracle_lib.product_batch(oracle_lib.OracleCode(code), lch[sample], L=4, cap=10**4, alpha=0.5, max_iter=20)
+    g = sg.unpack_bits(bits[sample], n)
+    first = r["half_iters"] == 1
+    np.testing.assert_array_equal(hi[sample][first], 1)
+    np.testing.assert_array_equal(q[sample][first], r["queries"][first])
+    same = (g == r["bits"]).reshape(len(sample), -1).all(axis=1)
+    assert same.mean() >= 0.9
+    # quality of the whole batch stays in the regime of the paper's (64,57)^2 curve
+    ferr = np.zeros(F, bool)
+    for lo in range(0, F, 10_000):
+        ferr[lo:lo + 10_000] = (sg.unpack_bits(bits[lo:lo + 10_000], n) != X[lo:lo + 10_000]).reshape(-1, n * n).any(1)
+    bler = [ferr[np.arange(F) % 7 == i].mean() for i in range(7)]
+    assert bler[0] > 0.1 and bler[2] < 0.01 and bler[6] < 1e-3
