@@ -40,6 +40,39 @@ L_LIST, CAP, ALPHA, MAX_ITER, SEED = 4, 10**4, 0.5, 20, 2310
 SMS, INT32_LANES = 152, 128  # GB300: 152 SMs x 128 INT32/FP32 lanes per SM
 METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 
+# DRAM bytes (read + write) per frame of k_product_persistent, from one ncu
+# capture of a 10,000-frame decode of this workload (traffic grows with the
+# frame count at a fixed Eb/N0 mix), valid only for the kernel sources whose
+# digest is recorded with it: `traffic` is null once they change.
+TRAFFIC = {"csrc_digest": "e62829059c3264b3ae2bd09ca1401a8f7e4e7096d808b78806ca63e471c9c00b",
+           "bytes_per_frame": 262192.0,
+           "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md"}
+
+
+def csrc_digest():
+    """SHA-256 of the CUDA sources (profiling-only #ifdef SG_PHASE_PROFILE blocks left out)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_2310_10737_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if not name.endswith((".cu", ".cuh", ".h")):
+            continue
+        keep, depth = [], 0
+        for line in open(os.path.join(d, name)):
+            t = line.strip()
+            if depth == 0 and t == "#ifdef SG_PHASE_PROFILE":
+                depth = 1
+                continue
+            if depth:
+                if t.startswith("#if"):
+                    depth += 1
+                elif t == "#endif":
+                    depth -= 1
+                continue
+            keep.append(line)
+        h.update(name.encode() + b"\0" + "".join(keep).encode())
+    return h.hexdigest()
+
 
 def log(msg):
     """Progress on stderr (the JSON line alone goes to stdout)."""
@@ -258,8 +291,12 @@ def main():
     sm_max = clk.get("sm_max_mhz") or 2070.0
     peak = SMS * INT32_LANES * sm_max * 1e6 / 1e12  # Tops/s
     achieved = ops / (t_half / 1000) / 1e12 if t_half > 0 else 0.0
+    traffic = None
+    if main_persistent and TRAFFIC["csrc_digest"] == csrc_digest():
+        traffic = TRAFFIC["bytes_per_frame"] * F
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                "frac": achieved / peak if peak else None, "traffic": None,
+                "frac": achieved / peak if peak else None, "traffic": traffic,
+                "traffic_source": TRAFFIC["source"] if traffic is not None else None,
                 "kernel": "k_product_persistent" if main_persistent else "k_product_half", "launches": half_launches,
                 "avg_launch_ms": t_half / max(half_launches, 1),
                 "ops_per_launch": ops / max(half_launches, 1),

@@ -127,6 +127,9 @@ template <int NPL, class SYN, bool COHERENT>
 __device__ __forceinline__ int product_word(const DevCode &code, const SisoParams &P, const ProductArgs &a,
                                             const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
+#ifdef SG_PHASE_PROFILE
+  const long long t0 = clock64();
+#endif
   const int n = code.n;
   const bool rows = (half & 1) != 0;
   const size_t fb = (size_t)f * n * n;
@@ -173,6 +176,12 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     if (used_xf && a.xf_count) atomicAdd(a.xf_count, 1);
   }
   __syncwarp();
+#ifdef SG_PHASE_PROFILE
+  if (lane == 0) {
+    SG_PROF(10, clock64() - t0);
+    SG_PROF(11, 1);
+  }
+#endif
   return res.queries;
 }
 

@@ -614,6 +614,9 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
     const float r = enz - tq;
     if (enz > 1e-30f && enz < 1e30f && r > 0.02f * (enz + tq)) return log2f(r);
   }
+#ifdef SG_PHASE_PROFILE
+  if (lane == 0) SG_PROF(6, 1);
+#endif
   const int Cs = __ldg(O.cost + tb + qs);
   const int R0 = min(max(Cs - c, 0), n);
   float g = CUDART_INF_F;
