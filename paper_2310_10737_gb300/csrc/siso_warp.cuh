@@ -20,16 +20,23 @@
 // keep the hits in query order, so list, stop point and query count are those
 // of a sequential decoder.
 //
-// Remaining mass.  The Corollary needs 1 - sum_{j <= q_L} p(z^j).  In FP32
-// that difference cancels catastrophically as soon as the queried mass
-// dominates, so the kernel sums the unqueried patterns directly (all terms
-// positive): patterns of cost above the stop level C* by a dynamic programme
-// over the ranks (cost-indexed, parity-split, a pattern is added to the tail
-// the moment one more rank lifts it over C*), plus the unqueried rest of
-// level C* from the table.  Masses are cost-scaled by exp(gamma * cost) so
-// that every factor stays <= 1; if the scaled total still falls below 2^-60
-// (all dominant terms underflow) or overflows, the same computation is redone
-// in an extended-range float (FP32 mantissa + int exponent).
+// Remaining mass.  The Corollary needs the mass of the unqueried patterns of
+// the parity class, i.e. the class total minus the queried mass.  Every
+// pattern mass is the product of per-rank factors t_e = exp(-|lambda_e|)
+// (one FP32 value per rank), and the queried masses are formed and summed in
+// double-float (an unevaluated pair of floats: Knuth's TwoSum and the
+// FMA-based exact product), so the difference is exact for those factors up
+// to about 2^-46 of the operands.  It is taken in FP32 when the remainder is
+// at least 2% of the operands, in double-float when it is at least 2^-26 of
+// them; below that (the list has taken nearly all the mass) the kernel sums
+// the unqueried patterns directly (all terms positive): patterns of cost above
+// the stop level C* by a dynamic programme over the ranks (cost-indexed,
+// parity-split, a pattern is added to the tail the moment one more rank lifts
+// it over C*), plus the unqueried rest of level C* from the table.  There the
+// masses are cost-scaled by exp(gamma * cost) so that every factor stays <= 1;
+// if the scaled total still falls below 2^-60 (all dominant terms underflow)
+// or overflows, the same computation is redone in an extended-range float
+// (FP32 mantissa + int exponent).
 #pragma once
 #include <cuda_runtime.h>
 #include <math_constants.h>
@@ -54,6 +61,49 @@ constexpr float LOG2E_F = 1.4426950408889634f;
 constexpr float LN2_F = 0.6931471805599453f;
 
 __host__ __device__ constexpr int align16(int x) { return (x + 15) & ~15; }
+
+// ----------------------------------------------------------------------------
+// double-float: value = h + l, |l| <= ulp(h) / 2 after df_norm.  Rounded
+// intrinsics keep the compiler from contracting the error terms.
+// ----------------------------------------------------------------------------
+struct DF {
+  float h, l;
+};
+__device__ __forceinline__ DF df_two_sum(float a, float b) {  // Knuth: s + err == a + b exactly
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+__device__ __forceinline__ DF df_norm(float h, float l) {  // |h| >= |l| (Dekker's fast two-sum)
+  const float s = __fadd_rn(h, l);
+  return {s, __fsub_rn(l, __fsub_rn(s, h))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = df_two_sum(a.h, b.h), t = df_two_sum(a.l, b.l);
+  const DF r = df_norm(s.h, __fadd_rn(s.l, t.h));
+  return df_norm(r.h, __fadd_rn(r.l, t.l));
+}
+__device__ __forceinline__ DF df_mul(DF a, DF b) {  // the FMA gives the exact error of a.h * b.h
+  const float p = __fmul_rn(a.h, b.h);
+  return df_norm(p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p))));
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  const float p = __fmul_rn(a.h, b);
+  return df_norm(p, fmaf(a.l, b, fmaf(a.h, b, -p)));
+}
+// running sum of nonnegative terms: the low part collects the exact rounding errors
+__device__ __forceinline__ void df_acc(DF &a, DF x) {
+  const DF s = df_two_sum(a.h, x.h);
+  a.h = s.h;
+  a.l = __fadd_rn(a.l, __fadd_rn(s.l, x.l));
+}
+__device__ __forceinline__ DF df_warp_sum(DF x) {  // lane 0's result broadcast (warp-uniform)
+  x = df_norm(x.h, x.l);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1)
+    x = df_add(x, DF{__shfl_xor_sync(0xffffffffu, x.h, d), __shfl_xor_sync(0xffffffffu, x.l, d)});
+  return {__shfl_sync(0xffffffffu, x.h, 0), __shfl_sync(0xffffffffu, x.l, 0)};
+}
 
 // ----------------------------------------------------------------------------
 // extended-range float: value = m * 2^e, m in [1, 2) (or 0)
@@ -128,11 +178,12 @@ struct XOps {  // extended range, unscaled
 // ----------------------------------------------------------------------------
 // per-warp shared-memory scratch
 // ----------------------------------------------------------------------------
-// H column and log2-mass of one reliability rank, read together in the query loop
+// H column and mass factor t = exp(-|lambda|) of one reliability rank, read
+// together in the query loop
 template <class SYN>
 struct RankRec {
   SYN h;
-  float l2;
+  float t;
 };
 
 template <int NPL, class SYN>
@@ -141,7 +192,7 @@ struct Layout {
   static constexpr int NM = (NT + 63) / 64;
   static constexpr int o_l2 = 0;                                      // float[NT] |lambda| log2(e), by rank
   static constexpr int o_al = o_l2 + 4 * NT;                          // float[NT] |lambda|, by rank
-  static constexpr int o_hr = o_al + 4 * NT;                          // RankRec[NT] H column + log2 mass, by rank
+  static constexpr int o_hr = o_al + 4 * NT;                          // RankRec[NT] H column + mass factor, by rank
   static constexpr int o_cw = align16(o_hr + (int)sizeof(RankRec<SYN>) * NT);  // u64[LMAX][NM] listed codewords
   static constexpr int o_lp = o_cw + 8 * LMAX * NM;                   // float[LMAX] log p(z)/p(0)
   static constexpr int o_wl = o_lp + 4 * LMAX;                        // float[LMAX] APP of each listed word
@@ -257,24 +308,28 @@ __device__ __forceinline__ int ent_rank(const uint4 &e) {
   return (wd >> (8 * (B & 3))) & 0xff;
 }
 
-// XOR of the rank-ordered H columns of a pattern and the sum of its ranks'
-// log2 masses (the loop runs to the warp's largest weight; shorter patterns
-// mask the extra terms)
+// XOR of the rank-ordered H columns of a pattern and its mass relative to
+// p(0), the product of its ranks' factors, in double-float (0 for the zero
+// pattern).  The loop runs to the warp's largest weight; shorter patterns
+// mask the extra terms.
 template <class SYN>
-__device__ __forceinline__ SYN ent_syndrome(const uint4 &e, int w, int wmax, const RankRec<SYN> *hr, float &l2sum) {
+__device__ __forceinline__ SYN ent_syndrome(const uint4 &e, int w, int wmax, const RankRec<SYN> *hr, DF &mass) {
   SYN s = 0;
-  float m = 0.f;
+  float mh = 1.f, ml = 0.f;
 #define SG_R(K)                                    \
   if (K < wmax) {                                  \
     const RankRec<SYN> v = hr[ent_rank<K>(e)];     \
     const bool on = K < w;                         \
     s ^= on ? v.h : (SYN)0;                        \
-    m += on ? v.l2 : 0.f;                          \
+    const float t = on ? v.t : 1.f;                \
+    const float p = __fmul_rn(mh, t);              \
+    ml = fmaf(ml, t, fmaf(mh, t, -p));             \
+    mh = p;                                        \
   }
   SG_R(0) SG_R(1) SG_R(2) SG_R(3) SG_R(4) SG_R(5) SG_R(6) SG_R(7)
   SG_R(8) SG_R(9) SG_R(10) SG_R(11) SG_R(12) SG_R(13) SG_R(14)
 #undef SG_R
-  l2sum = m;
+  mass = w > 0 ? DF{mh, ml} : DF{0.f, 0.f};
   return s;
 }
 
@@ -576,15 +631,47 @@ __device__ __noinline__ float remaining_log2_xf(const Scratch<NPL, SYN> &sc, con
   return __shfl_sync(FULL, xf_log2(x), 0);
 }
 
+// Class total of the nonzero patterns in double-float: prod_e (1 + y t_e) as
+// (even part - 1, odd part), lanes own ranks lane*NPL .. lane*NPL+NPL-1, then
+// a butterfly over the warp; lane 0's result is broadcast.
+template <int NPL, class SYN>
+__device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, int cls, int lane) {
+  DF u = {0.f, 0.f}, b = {0.f, 0.f};
+#pragma unroll
+  for (int k = 0; k < NPL; k++) {
+    const int e = lane * NPL + k;
+    if (e < n) {
+      const float t = sc.hr[e].t;
+      const DF nu = df_add(u, df_mul_f(b, t));
+      const DF nb = df_add(df_add(b, DF{t, 0.f}), df_mul_f(u, t));
+      u = nu;
+      b = nb;
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    const DF ou = {__shfl_xor_sync(FULL, u.h, d), __shfl_xor_sync(FULL, u.l, d)};
+    const DF ob = {__shfl_xor_sync(FULL, b.h, d), __shfl_xor_sync(FULL, b.l, d)};
+    const DF nu = df_add(df_add(u, ou), df_add(df_mul(u, ou), df_mul(b, ob)));
+    const DF nb = df_add(df_add(b, ob), df_add(df_mul(u, ob), df_mul(b, ou)));
+    u = nu;
+    b = nb;
+  }
+  const DF E = cls == 0 ? u : (cls == 1 ? b : df_add(u, b));
+  return {__shfl_sync(FULL, E.h, 0), __shfl_sync(FULL, E.l, 0)};
+}
+
 // log2 of the remaining (unqueried) mass relative to p(0^n|r); warp-uniform.
-// tq is the queried mass of the nonzero patterns (FP32, summed over the
-// warp).  When the class total minus tq is well conditioned (the difference
-// is at least 2% of the operands, so FP32 rounding of about 4e-6 of them
-// moves it by at most 2e-4 relative) that difference is used; otherwise the
+// tq is the queried mass of the nonzero patterns (double-float, summed over
+// the warp, the same value in every lane).  The class total minus tq is used
+// when it is well conditioned: in FP32 when the difference is at least 2% of
+// the operands (FP32 rounding of about 4e-6 of them moves it by at most 2e-4
+// relative), in double-float when it is at least 2^-26 of them (rounding of a
+// few 2^-46 moves it by at most about 1e-5 relative).  Otherwise the
 // unqueried patterns are summed directly.
 template <int NPL, class SYN>
 __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs, int n, int c,
-                                int cls, int lane, float tq, int *used_xf) {
+                                int cls, int lane, DF tq, int *used_xf) {
   // class total of the nonzero patterns: prod_e (1 + y t_e) as (even - 1, odd)
   {
     float u = 0.f, b = 0.f;
@@ -592,7 +679,7 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
     for (int k = 0; k < NPL; k++) {
       const int e = lane * NPL + k;
       if (e < n) {
-        const float t = exp2f(-sc.l2[e]);
+        const float t = sc.hr[e].t;
         const float nu = fmaf(b, t, u), nb = fmaf(u, t, b + t);
         u = nu;
         b = nb;
@@ -611,8 +698,21 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
     u = __shfl_sync(FULL, u, 0);
     b = __shfl_sync(FULL, b, 0);
     const float enz = cls == 0 ? u : (cls == 1 ? b : u + b);
-    const float r = enz - tq;
-    if (enz > 1e-30f && enz < 1e30f && r > 0.02f * (enz + tq)) return log2f(r);
+    const float tqf = tq.h + tq.l;
+    const float r = enz - tqf;
+    const bool in_range = enz > 0x1p-60f && enz < 0x1p60f;
+    if (in_range && r > 0.02f * (enz + tqf)) return log2f(r);
+    if (in_range) {
+      const DF E = class_total_df<NPL, SYN>(sc, n, cls, lane);
+      const DF R = df_add(E, DF{-tq.h, -tq.l});
+#ifdef SG_PHASE_PROFILE
+      if (lane == 0) SG_PROF(R.h > 0x1p-26f * (E.h + tq.h) ? 12 : 13, 1);
+#endif
+      if (R.h > 0x1p-26f * (E.h + tq.h)) return log2f(R.h + R.l);
+    }
+#ifdef SG_PHASE_PROFILE
+    if (!in_range && lane == 0) SG_PROF(15, 1);
+#endif
   }
 #ifdef SG_PHASE_PROFILE
   if (lane == 0) SG_PROF(6, 1);
@@ -698,10 +798,11 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
     if (e < n) {
       const float a = __uint_as_float((unsigned)(key[k] >> 32));
       const int idx = (int)(key[k] & 0xffffffffu);
+      const float l2v = __fmul_rn(a, LOG2E_F);
       sc.al[e] = a;
-      sc.l2[e] = a * LOG2E_F;
+      sc.l2[e] = l2v;
       sc.perm[e] = (uint8_t)idx;
-      sc.hr[e] = RankRec<SYN>{(SYN)__ldg(code.hcol + idx), a * LOG2E_F};
+      sc.hr[e] = RankRec<SYN>{(SYN)__ldg(code.hcol + idx), exp2f(-l2v)};
       const int64_t qa = quant256(a);
       sy += qa;
       sxy += qa * (e + 1);
@@ -858,7 +959,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   float lr2 = 0.f;  // log2 remaining mass (set when the search stops)
   bool have_lr2 = false;
   int wacc = 0;       // this lane's share of the summed pattern weights
-  float tmass = 0.f;  // this lane's share of the queried mass (nonzero patterns)
+  DF tmass = {0.f, 0.f};  // this lane's share of the queried mass (nonzero patterns)
   for (;;) {
     const int lim = min(32, qlim - q);
     if (lim <= 0) break;
@@ -869,9 +970,8 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     if (lane < lim) e = __ldg(O.ent + tb + q + lane);
     const int w = e.x & 0xff;
     const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
-    float l2sum;
-    const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr, l2sum) ^ h.s0;
-    const float mass = w > 0 ? exp2f(-l2sum) : 0.f;
+    DF mass;
+    const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr, mass) ^ h.s0;
     const bool hit = lane < lim && s == 0;
     unsigned hm = __ballot_sync(FULL, hit);
     int stop_lane = -1;
@@ -885,7 +985,9 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
         break;
       }
       if (P.thr > 0.f) {
-        const float tq = __shfl_sync(FULL, warp_sum_f(tmass + (lane <= hl ? mass : 0.f)), 0);
+        DF part = tmass;
+        if (lane <= hl) df_acc(part, mass);
+        const DF tq = df_warp_sum(part);
         const float r2 = remaining_log2<NPL, SYN>(sc, O, tb, tc, q + hl, n, h.c, cls, lane, tq, xf_count);
         if (thr_reached(sc, nhit, r2 * LN2_F + code.log_phi, P.thr)) {
           stop_lane = hl;
@@ -898,13 +1000,13 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     if (stop_lane >= 0) {
       if (lane <= stop_lane) {
         wacc += w;
-        tmass += mass;
+        df_acc(tmass, mass);
       }
       q += stop_lane + 1;
       break;
     }
     wacc += w;  // lanes past lim hold an empty entry
-    tmass += mass;
+    df_acc(tmass, mass);
     q += lim;
   }
   // the whole parity class has been queried: nothing remains
@@ -917,8 +1019,8 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   // soft output (Corollary + eq. LLRi)
   if (!have_lr2)
     lr2 = exhausted ? -CUDART_INF_F
-                    : remaining_log2<NPL, SYN>(sc, O, tb, tc, q - 1, n, h.c, cls, lane,
-                                               __shfl_sync(FULL, warp_sum_f(tmass), 0), xf_count);
+                    : remaining_log2<NPL, SYN>(sc, O, tb, tc, q - 1, n, h.c, cls, lane, df_warp_sum(tmass),
+                                               xf_count);
 #ifdef SG_PHASE_PROFILE
   const long long t3 = clock64();
 #endif
