@@ -178,7 +178,8 @@ int product_decode_ex(sogrand_code *row_code, const sogrand_code *col_code, int6
  * frames are unfinished the kernel stops and the call returns
  * SOGRAND_ETIMEOUT.  stats->timing_ms[0] is the kernel's device time;
  * launches counts 2 (queue set-up and the decoder).  Scratch, allocated
- * stream-ordered: about 4 n^2 + 8 n ceil(n/64) + 36 bytes per frame.  The
+ * stream-ordered from the library's pool (see sogrand_release_cached): about
+ * 4 n^2 + 8 n ceil(n/64) + 8 max_iter + 37 bytes per frame.  The
  * call synchronises `stream` at its end to read the kernel's status.
  * Errors: as product_decode_ex, plus ETIMEOUT; EINVAL also if
  * n_frames * 2 * max_iter >= 2^31.
@@ -191,9 +192,13 @@ int product_decode_persistent(sogrand_code *row_code, const sogrand_code *col_co
 /*
  * product_decode on HOST buffers: copies llr_ch to the device, decodes with
  * the batched form (product_decode_persistent) and copies the results back
- * before returning (device buffers are allocated
- * stream-ordered on `stream` and freed before return).  Pinned host memory
- * makes the copies asynchronous DMA; pageable memory works too.
+ * before returning.  Batches of 4096 frames or more are split into up to 8
+ * chunks whose host-to-device copy, decoding (two internal streams, chunks in
+ * turn) and device-to-host copy overlap; the internal streams start after the
+ * work already queued on `stream`, and `stream` is synchronised before the
+ * call returns.  Device buffers come from the library's memory pool and are
+ * freed before return.  Pinned host memory makes the copies asynchronous DMA
+ * (and lets them overlap decoding); pageable memory works too.
  *   llr_ch     HOST [n_frames][n][n]
  *   bits       HOST [n_frames][ceil(n*n/8)] (required)
  *   half_iters, status, queries  HOST [n_frames] (each may be NULL)
@@ -253,6 +258,16 @@ int product_decode_noalloc(sogrand_code *row_code, const sogrand_code *col_code,
  */
 int sogrand_trace_patterns(sogrand_code *code, const float *llr, int64_t max_q, uint64_t *patterns_out,
                            int64_t *n_out, int32_t *c_out);
+
+/*
+ * Device scratch of the decoders (the per-frame L_E state and counters) comes
+ * from one stream-ordered memory pool per device that the library creates on
+ * first use and that keeps freed memory for the next call.  This returns the
+ * idle memory of every such pool to the device.  Call it once the streams
+ * that used the library are synchronised (memory whose stream-ordered free
+ * has not yet run stays in the pool).  Errors: ECUDA.
+ */
+int sogrand_release_cached(void);
 
 /* Static text for an error code. */
 const char *sogrand_strerror(int err);

@@ -5,13 +5,13 @@ Public entry points (same names as the C ABI in include/sogrand.h):
 * :class:`Code` / :func:`sogrand_code_create` -- a component code from H;
 * :func:`sogrand_decode` -- SISO decoding of many independent words;
 * :func:`product_decode` -- block turbo decoding of product codes;
-* :func:`sogrand_trace_patterns` -- the device's canonical query order (test hook).
+* :func:`sogrand_trace_patterns` -- the device's canonical query order (test hook);
+* :func:`sogrand_release_cached` -- hand the decoders' pooled scratch back to the device.
 
 All compute runs in hand-written CUDA kernels for sm_103a (libsogrand.so);
 PyTorch only provides device memory and streams.
 """
 from ._lib import (  # noqa: F401
     Code, LIB_PATH, ProductStats, SograndError, load, product_decode, product_decode_host, sogrand_code_create,
-    sogrand_decode,
-    sogrand_trace_patterns, strerror, unpack_bits, unpack_words,
+    sogrand_decode, sogrand_release_cached, sogrand_trace_patterns, strerror, unpack_bits, unpack_words,
 )

@@ -58,11 +58,12 @@ def load() -> C.CDLL:
         L.product_decode_persistent.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp,
                                                 C.POINTER(ProductStats), vp]
         L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
+        L.sogrand_release_cached.argtypes = []
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
-                     "sogrand_trace_patterns"):
+                     "sogrand_trace_patterns", "sogrand_release_cached"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -214,6 +215,11 @@ def product_decode_host(code: Code, llr_ch: np.ndarray, L: int = 4, query_cap: i
                                     hp(out["status"]), hp(out["queries"]), _stream(stream))
     _check(rc, "product_decode_host")
     return out
+
+
+def sogrand_release_cached():
+    """Return the idle memory of the library's device pools (call after synchronising)."""
+    _check(load().sogrand_release_cached(), "sogrand_release_cached")
 
 
 def unpack_bits(bits, n: int):

@@ -295,6 +295,45 @@ bool ones_in_rowspace(int n, int m, const uint8_t *H) {
     }                                                                      \
   } while (0)
 
+// ---------------------------------------------------------------------------
+// device scratch: one stream-ordered memory pool per device, owned by the
+// library.  It keeps its memory between calls (release threshold: never), so
+// the per-frame L_E state (4 n^2 bytes a frame, gigabytes for a large batch)
+// is not unmapped and mapped again on every decode.  sogrand_release_cached
+// hands the idle memory back.
+// ---------------------------------------------------------------------------
+constexpr int MAX_DEV = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[MAX_DEV] = {};
+
+cudaError_t scratch_alloc(char **p, size_t bytes, cudaStream_t s) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= MAX_DEV) return cudaErrorInvalidDevice;
+  cudaMemPool_t pool = nullptr;
+  {
+    std::lock_guard<std::mutex> g(g_pool_mu);
+    if (!g_pool[dev]) {
+      cudaMemPoolProps pp{};
+      pp.allocType = cudaMemAllocationTypePinned;
+      pp.handleTypes = cudaMemHandleTypeNone;
+      pp.location.type = cudaMemLocationTypeDevice;
+      pp.location.id = dev;
+      e = cudaMemPoolCreate(&g_pool[dev], &pp);
+      if (e != cudaSuccess) {
+        g_pool[dev] = nullptr;
+        return e;
+      }
+      uint64_t keep = UINT64_MAX;
+      e = cudaMemPoolSetAttribute(g_pool[dev], cudaMemPoolAttrReleaseThreshold, &keep);
+      if (e != cudaSuccess) return e;
+    }
+    pool = g_pool[dev];
+  }
+  return cudaMallocFromPoolAsync((void **)p, bytes, pool, s);
+}
+
 int ensure_cap(sogrand_code *c, int64_t cap) {
   std::lock_guard<std::mutex> g(c->mu);
   int dev = 0;
@@ -314,6 +353,13 @@ int scratch_bytes(int npl, int syn_bytes, int jmax) {
 }  // namespace sg
 
 extern "C" {
+
+int sogrand_release_cached(void) {
+  std::lock_guard<std::mutex> g(g_pool_mu);
+  for (int d = 0; d < MAX_DEV; d++)
+    if (g_pool[d] && cudaMemPoolTrimTo(g_pool[d], 0) != cudaSuccess) return SOGRAND_ECUDA;
+  return SOGRAND_OK;
+}
 
 const char *sogrand_strerror(int err) {
   switch (err) {
@@ -438,7 +484,7 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   const size_t total = al(b_le) + al(b_hb) + 2 * al(b_i32) + (half_iters ? 0 : al(b_i32)) +
                        (queries ? 0 : al(b_i64)) + (par_queries ? 0 : al(b_i64)) + (status ? 0 : al((size_t)F)) + 256;
   char *mem = nullptr;
-  if (cudaMallocAsync((void **)&mem, total, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  if (scratch_alloc(&mem, total, s) != cudaSuccess) return SOGRAND_ENOMEM;
   char *p = mem;
   auto take = [&p, &al](size_t bytes) {
     char *r = p;
@@ -507,74 +553,118 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   return SOGRAND_OK;
 }
 
-int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
-                              int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
-                              uint8_t *status, int64_t *queries, product_decode_stats *stats, void *stream) {
-  int64_t *par_queries = stats ? stats->par_queries : nullptr;
-  if (stats && stats->timing_ms) stats->timing_ms[0] = stats->timing_ms[1] = 0.f;
-  if (stats && stats->launches) stats->launches[0] = 0;
+}  // extern "C"
+
+namespace {
+
+// Argument checks shared by the batched entry points.
+int persistent_check(const sogrand_code *rc_, const sogrand_code *cc_, int64_t F, int L, int64_t cap, float thr,
+                     float alpha, int max_iter) {
   if (!rc_ || !cc_ || F < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f) ||
       !(alpha > 0.f && alpha < 1e6f) || max_iter < 1 || max_iter > 1000)
     return SOGRAND_EINVAL;
   if (rc_ != cc_) return SOGRAND_EUNSUPPORTED;
-  sogrand_code *c = rc_;
-  if (c->n - 1 < 63 && cap >= (int64_t(1) << (c->n - 1))) return SOGRAND_EINVAL;
-  if (F == 0) return SOGRAND_OK;
-  if (!llr_ch || !bits) return SOGRAND_EINVAL;
+  if (rc_->n - 1 < 63 && cap >= (int64_t(1) << (rc_->n - 1))) return SOGRAND_EINVAL;
   // word tickets (slots x n, plus one per idle warp) are 32-bit
   if (F * 2 * (int64_t)max_iter * rc_->n >= (int64_t(1) << 31) - (int64_t(1) << 22)) return SOGRAND_EINVAL;
-  int rc = ensure_cap(c, cap);
-  if (rc != SOGRAND_OK) return rc;
-  cudaStream_t s = (cudaStream_t)stream;
-  const int n = c->n, nm = c->nm;
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t b_le = (size_t)F * n * n * sizeof(float), b_hb = (size_t)F * n * nm * sizeof(uint64_t);
+  return SOGRAND_OK;
+}
+
+inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+
+// Scratch of one batched decode of F frames: L_E state, hard decisions, the
+// per-frame counters, the frame-half list, room for every optional output and
+// the control words.  Every sub-buffer starts on a 256-byte boundary.
+size_t persistent_scratch_bytes(int64_t F, int n, int nm, int max_iter) {
   const size_t b_i32 = (size_t)F * sizeof(int32_t), b_i64 = (size_t)F * sizeof(int64_t);
-  const size_t b_queue = (size_t)F * 2 * max_iter * sizeof(int32_t);
-  const size_t total = al(b_le) + al(b_hb) + 4 * al(b_i32) + al(b_queue) + (half_iters ? 0 : al(b_i32)) +
-                       (queries ? 0 : al(b_i64)) + (par_queries ? 0 : al(b_i64)) + (status ? 0 : al((size_t)F)) +
-                       al(4 * sizeof(int32_t));
-  char *mem = nullptr;
-  if (cudaMallocAsync((void **)&mem, total, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  return al256((size_t)F * n * n * sizeof(float)) + al256((size_t)F * n * nm * sizeof(uint64_t)) + 5 * al256(b_i32) +
+         al256((size_t)F * 2 * max_iter * sizeof(int32_t)) + 2 * al256(b_i64) + al256((size_t)F) +
+         al256(4 * sizeof(int32_t));
+}
+
+// Queue set-up and the persistent kernel for F frames on stream s (nothing
+// is waited for).  Outputs that are null go to the scratch.  *err_dev is the
+// device word that holds the kernel's timeout flag afterwards.
+cudaError_t persistent_enqueue(sogrand_code *c, int64_t F, const float *llr_ch, const sg::SisoParams &P, float alpha,
+                               int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
+                               int64_t *par_queries, unsigned long long *wsum, int32_t *xf, char *mem,
+                               cudaStream_t s, int32_t **err_dev) {
+  const int n = c->n, nm = c->nm;
   char *p = mem;
-  auto take = [&p, &al](size_t bytes) {
+  auto take = [&p](size_t bytes) {
     char *r = p;
-    p += al(bytes);
+    p += al256(bytes);
     return r;
   };
+  const size_t b_i32 = (size_t)F * sizeof(int32_t), b_i64 = (size_t)F * sizeof(int64_t);
   sg::ProductArgs a{};
   a.n_frames = F;
   a.llr_ch = llr_ch;
   a.alpha = alpha;
   a.max_half = 2 * max_iter;
-  a.le = (float *)take(b_le);
-  a.hb = (uint64_t *)take(b_hb);
+  a.le = (float *)take((size_t)F * n * n * sizeof(float));
+  a.hb = (uint64_t *)take((size_t)F * n * nm * sizeof(uint64_t));
   a.hmax = (int32_t *)take(b_i32);
   a.half_cur = (int32_t *)take(b_i32);
   a.done_words = (int32_t *)take(b_i32);
   a.bad = (int32_t *)take(b_i32);
-  a.queue = (int32_t *)take(b_queue);
-  a.bits = bits;
-  a.half_iters = half_iters ? half_iters : (int32_t *)take(b_i32);
-  a.queries = queries ? queries : (int64_t *)take(b_i64);
-  a.par_queries = par_queries ? par_queries : (int64_t *)take(b_i64);
-  a.status = status ? status : (uint8_t *)take((size_t)F);
+  a.queue = (int32_t *)take((size_t)F * 2 * max_iter * sizeof(int32_t));
+  int32_t *hi_s = (int32_t *)take(b_i32);
+  int64_t *q_s = (int64_t *)take(b_i64);
+  int64_t *pq_s = (int64_t *)take(b_i64);
+  uint8_t *st_s = (uint8_t *)take((size_t)F);
   a.ctrl = (int32_t *)take(4 * sizeof(int32_t));
+  a.bits = bits;
+  a.half_iters = half_iters ? half_iters : hi_s;
+  a.queries = queries ? queries : q_s;
+  a.par_queries = par_queries ? par_queries : pq_s;
+  a.status = status ? status : st_s;
   a.max_spin = 2000000;  // 2 s of back-off without any work
-  a.xf_count = stats ? stats->xf_words : nullptr;
-  a.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
+  a.xf_count = xf;
+  a.wsum = wsum;
+  *err_dev = a.ctrl + 3;
   sg::DevCode d = dev_code(c);
-  sg::SisoParams P{L, (int32_t)cap, thr};
+  cudaError_t e = cudaSuccess;
+  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, P, a, s)));
+  return e;
+}
+
+}  // namespace
+
+extern "C" {
+
+int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
+                              int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                              uint8_t *status, int64_t *queries, product_decode_stats *stats, void *stream) {
+  if (stats && stats->timing_ms) stats->timing_ms[0] = stats->timing_ms[1] = 0.f;
+  if (stats && stats->launches) stats->launches[0] = 0;
+  int rc = persistent_check(rc_, cc_, F, L, cap, thr, alpha, max_iter);
+  if (rc != SOGRAND_OK) return rc;
+  if (F == 0) return SOGRAND_OK;
+  if (!llr_ch || !bits) return SOGRAND_EINVAL;
+  sogrand_code *c = rc_;
+  rc = ensure_cap(c, cap);
+  if (rc != SOGRAND_OK) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  char *mem = nullptr;
+  if (scratch_alloc(&mem, persistent_scratch_bytes(F, c->n, c->nm, max_iter), s) != cudaSuccess)
+    return SOGRAND_ENOMEM;
+  const sg::SisoParams P{L, (int32_t)cap, thr};
   const bool timed = stats && stats->timing_ms;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaError_t e = cudaSuccess;
   if (timed)
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
   if (e == cudaSuccess && timed) e = cudaEventRecord(ev[0], s);
-  if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, P, a, s)));
+  int32_t *err_dev = nullptr;
+  if (e == cudaSuccess)
+    e = persistent_enqueue(c, F, llr_ch, P, alpha, max_iter, bits, half_iters, status, queries,
+                           stats ? stats->par_queries : nullptr,
+                           stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr,
+                           stats ? stats->xf_words : nullptr, mem, s, &err_dev);
   if (e == cudaSuccess && timed) e = cudaEventRecord(ev[1], s);
   int32_t err = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, a.ctrl + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && timed) {
     float x = 0.f;
@@ -592,36 +682,90 @@ int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_
 int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
                         int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
                         uint8_t *status, int64_t *queries, void *stream) {
-  if (!rc_ || F < 0) return SOGRAND_EINVAL;
+  int rc = persistent_check(rc_, cc_, F, L, cap, thr, alpha, max_iter);
+  if (rc != SOGRAND_OK) return rc;
   if (F == 0) return SOGRAND_OK;
   if (!llr_ch || !bits) return SOGRAND_EINVAL;
+  sogrand_code *c = rc_;
+  rc = ensure_cap(c, cap);
+  if (rc != SOGRAND_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = rc_->n;
-  const size_t b_in = (size_t)F * n * n * sizeof(float), nb = ((size_t)n * n + 7) / 8, b_bits = (size_t)F * nb;
-  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
-  const size_t total = al(b_in) + al(b_bits) + al((size_t)F * 4) + al((size_t)F) + al((size_t)F * 8);
+  const int n = c->n, nm = c->nm;
+  const size_t in_f = (size_t)n * n * sizeof(float), nb = ((size_t)n * n + 7) / 8;
+  // Chunks of the batch move through three stages on their own streams:
+  // copy in (h2d), decode (two streams taking chunks in turn, so the tail of
+  // one chunk overlaps the start of the next), copy out (d2h).  Events order
+  // the stages of each chunk; all streams start after the caller's stream.
+  const int64_t K = std::max<int64_t>(1, std::min<int64_t>(8, F / 2048));
+  const int64_t chunk = (F + K - 1) / K;
+  const size_t b_in = al256((size_t)F * in_f), b_bits = al256((size_t)F * nb);
+  const size_t b_out = b_in + b_bits + al256((size_t)F * 4) + al256((size_t)F) + al256((size_t)F * 8);
+  const size_t b_scr = al256(persistent_scratch_bytes(chunk, n, nm, max_iter));
   char *mem = nullptr;
-  if (cudaMallocAsync((void **)&mem, total, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  if (scratch_alloc(&mem, b_out + 2 * b_scr + 256, s) != cudaSuccess) return SOGRAND_ENOMEM;
   float *d_in = (float *)mem;
-  uint8_t *d_bits = (uint8_t *)(mem + al(b_in));
-  int32_t *d_hi = (int32_t *)(mem + al(b_in) + al(b_bits));
-  uint8_t *d_st = (uint8_t *)(mem + al(b_in) + al(b_bits) + al((size_t)F * 4));
-  int64_t *d_q = (int64_t *)(mem + al(b_in) + al(b_bits) + al((size_t)F * 4) + al((size_t)F));
-  int rc = SOGRAND_OK;
-  if (cudaMemcpyAsync(d_in, llr_ch, b_in, cudaMemcpyHostToDevice, s) != cudaSuccess) rc = SOGRAND_ECUDA;
-  if (rc == SOGRAND_OK)
-    rc = product_decode_persistent(rc_, cc_, F, d_in, L, cap, thr, alpha, max_iter, d_bits, d_hi, d_st, d_q, nullptr,
-                                   stream);
-  if (rc == SOGRAND_OK) {
-    cudaError_t e = cudaMemcpyAsync(bits, d_bits, b_bits, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && half_iters) e = cudaMemcpyAsync(half_iters, d_hi, (size_t)F * 4, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status, d_st, (size_t)F, cudaMemcpyDeviceToHost, s);
-    if (e == cudaSuccess && queries) e = cudaMemcpyAsync(queries, d_q, (size_t)F * 8, cudaMemcpyDeviceToHost, s);
-    if (e != cudaSuccess) rc = SOGRAND_ECUDA;
+  uint8_t *d_bits = (uint8_t *)(mem + b_in);
+  int32_t *d_hi = (int32_t *)(mem + b_in + b_bits);
+  uint8_t *d_st = (uint8_t *)(mem + b_in + b_bits + al256((size_t)F * 4));
+  int64_t *d_q = (int64_t *)(mem + b_in + b_bits + al256((size_t)F * 4) + al256((size_t)F));
+  int32_t *d_err = (int32_t *)(mem + b_out + 2 * b_scr);  // one timeout flag per chunk (K <= 8)
+  const sg::SisoParams P{L, (int32_t)cap, thr};
+  cudaStream_t st[4] = {nullptr, nullptr, nullptr, nullptr};  // h2d, decode x2, d2h
+  std::vector<cudaEvent_t> ev;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaStreamCreateWithFlags(&st[i], cudaStreamNonBlocking);
+  auto event = [&ev, &e]() {
+    cudaEvent_t x = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (x) ev.push_back(x);
+    return x;
+  };
+  cudaEvent_t start = event();
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, 8 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaEventRecord(start, s);
+  for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaStreamWaitEvent(st[i], start, 0);
+  for (int64_t k = 0; k < K && e == cudaSuccess; k++) {
+    const int64_t f0 = k * chunk, Fk = std::min(chunk, F - f0);
+    if (Fk <= 0) break;
+    cudaStream_t sd = st[1 + (k & 1)];
+    cudaEvent_t in_done = event(), dec_done = event();
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync((char *)d_in + f0 * in_f, (const char *)llr_ch + f0 * in_f, Fk * in_f,
+                          cudaMemcpyHostToDevice, st[0]);
+    if (e == cudaSuccess) e = cudaEventRecord(in_done, st[0]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(sd, in_done, 0);
+    int32_t *err_k = nullptr;
+    if (e == cudaSuccess)
+      e = persistent_enqueue(c, Fk, (const float *)((const char *)d_in + f0 * in_f), P, alpha, max_iter,
+                             d_bits + f0 * nb, d_hi + f0, d_st + f0, d_q + f0, nullptr, nullptr, nullptr,
+                             mem + b_out + (k & 1) * b_scr, sd, &err_k);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_err + k, err_k, sizeof(int32_t), cudaMemcpyDeviceToDevice, sd);
+    if (e == cudaSuccess) e = cudaEventRecord(dec_done, sd);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st[3], dec_done, 0);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(bits + f0 * nb, d_bits + f0 * nb, Fk * nb, cudaMemcpyDeviceToHost, st[3]);
+    if (e == cudaSuccess && half_iters)
+      e = cudaMemcpyAsync(half_iters + f0, d_hi + f0, Fk * 4, cudaMemcpyDeviceToHost, st[3]);
+    if (e == cudaSuccess && status) e = cudaMemcpyAsync(status + f0, d_st + f0, Fk, cudaMemcpyDeviceToHost, st[3]);
+    if (e == cudaSuccess && queries)
+      e = cudaMemcpyAsync(queries + f0, d_q + f0, Fk * 8, cudaMemcpyDeviceToHost, st[3]);
   }
-  if (cudaFreeAsync(mem, s) != cudaSuccess && rc == SOGRAND_OK) rc = SOGRAND_ECUDA;
-  if (cudaStreamSynchronize(s) != cudaSuccess && rc == SOGRAND_OK) rc = SOGRAND_ECUDA;
-  return rc;
+  int32_t err[8] = {0};
+  if (e == cudaSuccess) e = cudaMemcpyAsync(err, d_err, sizeof(err), cudaMemcpyDeviceToHost, st[3]);
+  // the caller's stream resumes after every stage
+  for (int i = 0; i < 4 && st[i]; i++) {
+    cudaEvent_t x = event();
+    if (e == cudaSuccess) e = cudaEventRecord(x, st[i]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, x, 0);
+  }
+  cudaError_t e2 = cudaFreeAsync(mem, s);
+  cudaError_t e3 = cudaStreamSynchronize(s);
+  for (cudaEvent_t x : ev) cudaEventDestroy(x);
+  for (int i = 0; i < 4; i++)
+    if (st[i]) cudaStreamDestroy(st[i]);
+  if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return SOGRAND_ECUDA;
+  for (int k = 0; k < 8; k++)
+    if (err[k]) return SOGRAND_ETIMEOUT;
+  return SOGRAND_OK;
 }
 
 int product_decode(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch, int L,

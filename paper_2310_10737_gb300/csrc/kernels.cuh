@@ -119,13 +119,25 @@ __device__ __forceinline__ uint64_t ld_state(const uint64_t *p) {
   return *p;
 }
 
+// Per-warp tallies flushed to the global counters once, when the warp exits.
+struct WarpTally {
+  unsigned long long wsum = 0;  // summed pattern weights
+  int xf = 0;                   // words that took the extended-range path
+  __device__ void flush(const ProductArgs &a, int lane) const {
+    if (lane != 0) return;
+    if (a.wsum && wsum) atomicAdd(a.wsum, wsum);
+    if (a.xf_count && xf) atomicAdd(a.xf_count, xf);
+  }
+};
+
 // One component word of frame f in half `half` (rows when odd): lambda =
 // L_Ch + fl32(alpha L_E) (L_A = 0 in the first half), SOGRAND, then L_E and
 // the hard decision of L_APP are stored and the query counters updated.
 // Returns the word's query count (-1: non-finite input).
 template <int NPL, class SYN, bool COHERENT>
 __device__ __forceinline__ int product_word(const DevCode &code, const SisoParams &P, const ProductArgs &a,
-                                            const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane) {
+                                            const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane,
+                                            WarpTally &tally) {
   constexpr int NM = (32 * NPL + 63) / 64;
 #ifdef SG_PHASE_PROFILE
   const long long t0 = clock64();
@@ -171,9 +183,9 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     if (res.queries >= 0) {
       atomicAdd(reinterpret_cast<unsigned long long *>(a.queries + f), (unsigned long long)res.queries);
       atomicMax(a.hmax + f, res.queries);
-      if (a.wsum) atomicAdd(a.wsum, (unsigned long long)res.wsum);
+      tally.wsum += (unsigned long long)res.wsum;
     }
-    if (used_xf && a.xf_count) atomicAdd(a.xf_count, 1);
+    tally.xf += used_xf;
   }
   __syncwarp();
 #ifdef SG_PHASE_PROFILE
@@ -292,15 +304,17 @@ __global__ void __launch_bounds__(TPB, 6) k_product_half(const DevCode code, con
   const int n = code.n;
   const int64_t items = a.n_frames * n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
+  WarpTally tally;
   for (int64_t it = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp; it < items; it += nwarps) {
     const int64_t f = it / n;
     const int wd = (int)(it - f * n);
     const int32_t fs = __ldg(a.fstate + f);
     if (fs != F_RUN && fs != F_BAD_PENDING) continue;  // finished frames only: a flag raised during
                                                         // this half must not change which words run
-    const int q = product_word<NPL, SYN, false>(code, P, a, sc, f, wd, half, lane);
+    const int q = product_word<NPL, SYN, false>(code, P, a, sc, f, wd, half, lane, tally);
     if (lane == 0 && q < 0) atomicExch(a.fstate + f, (int32_t)F_BAD_PENDING);
   }
+  tally.flush(a, lane);
 }
 
 // One warp per frame.
@@ -365,6 +379,7 @@ __global__ void __launch_bounds__(TPB, 6) k_product_persistent(const DevCode cod
   uint64_t *R = W + NT * NM;
   // Every read of shared scheduling state is made by lane 0 and broadcast, so
   // the whole warp always takes the same branch.
+  WarpTally tally;
   for (;;) {
     int ticket = 0;
     if (lane == 0) ticket = atomicAdd(a.ctrl + 1, 1);
@@ -402,7 +417,7 @@ __global__ void __launch_bounds__(TPB, 6) k_product_persistent(const DevCode cod
     int half = 0;
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
-    const int q = product_word<NPL, SYN, true>(code, P, a, sc, f, w, half, lane);
+    const int q = product_word<NPL, SYN, true>(code, P, a, sc, f, w, half, lane, tally);
     if (lane == 0 && q < 0) atomicExch(a.bad + f, 1);
     __threadfence();  // release this word's L_E and hard decision
     __syncwarp();
@@ -436,6 +451,7 @@ __global__ void __launch_bounds__(TPB, 6) k_product_persistent(const DevCode cod
     }
     __syncwarp();
   }
+  tally.flush(a, lane);
 }
 
 // list and counters of the persistent form: every frame queued for half 1

@@ -83,6 +83,11 @@ __device__ __forceinline__ DF df_add(DF a, DF b) {
   const DF r = df_norm(s.h, __fadd_rn(s.l, t.h));
   return df_norm(r.h, __fadd_rn(r.l, t.l));
 }
+// a + b for a, b >= 0 (no cancellation: one TwoSum on the high parts)
+__device__ __forceinline__ DF df_add_pos(DF a, DF b) {
+  const DF s = df_two_sum(a.h, b.h);
+  return df_norm(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
 __device__ __forceinline__ DF df_mul(DF a, DF b) {  // the FMA gives the exact error of a.h * b.h
   const float p = __fmul_rn(a.h, b.h);
   return df_norm(p, fmaf(a.h, b.l, fmaf(a.l, b.h, fmaf(a.h, b.h, -p))));
@@ -97,11 +102,11 @@ __device__ __forceinline__ void df_acc(DF &a, DF x) {
   a.h = s.h;
   a.l = __fadd_rn(a.l, __fadd_rn(s.l, x.l));
 }
-__device__ __forceinline__ DF df_warp_sum(DF x) {  // lane 0's result broadcast (warp-uniform)
+__device__ __forceinline__ DF df_warp_sum(DF x) {  // x >= 0; lane 0's result broadcast (warp-uniform)
   x = df_norm(x.h, x.l);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1)
-    x = df_add(x, DF{__shfl_xor_sync(0xffffffffu, x.h, d), __shfl_xor_sync(0xffffffffu, x.l, d)});
+    x = df_add_pos(x, DF{__shfl_xor_sync(0xffffffffu, x.h, d), __shfl_xor_sync(0xffffffffu, x.l, d)});
   return {__shfl_sync(0xffffffffu, x.h, 0), __shfl_sync(0xffffffffu, x.l, 0)};
 }
 
@@ -296,8 +301,15 @@ __device__ __forceinline__ int one_line_c(int64_t sy, int64_t sxy, int n, int c_
   int64_t num = sy * D - Nb * sx;
   int64_t top = 2 * num + (int64_t)n * Nb;
   if (top < 0) return 0;
-  int64_t c = top / (2 * (int64_t)n * Nb);
-  return (int)(c > c_max ? c_max : c);
+  // floor(top / den) clamped to c_max: an FP32 estimate corrected with exact
+  // integer products (the quotient that matters is at most c_max <= 128)
+  const int64_t den = 2 * (int64_t)n * Nb;
+  if (top >= (int64_t)(c_max + 1) * den) return c_max;
+  int64_t c = (int64_t)((float)top / (float)den);
+  c = c < 0 ? 0 : (c > c_max ? c_max : c);
+  while (c > 0 && c * den > top) c--;
+  while (c < c_max && (c + 1) * den <= top) c++;
+  return (int)c;
 }
 
 // rank k (0-based position in the pattern) of a table entry: byte k + 1
@@ -501,7 +513,7 @@ __device__ __noinline__ void dp_smem(int Cs, int c, int R0, int cls, const typen
 // carries the factor 2^(g2 * Cs) (g2 = gamma log2 e); with XOps g2 = 0.
 // `qs` is the order-table index of the last queried pattern.
 template <class Ops, int NPL, class SYN>
-__device__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs,
+__device__ __noinline__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs,
                                             int n, int c, int cls, int Cs, float g2, int lane) {
   using T = typename Ops::T;
   constexpr int NT = 32 * NPL;
@@ -633,7 +645,8 @@ __device__ __noinline__ float remaining_log2_xf(const Scratch<NPL, SYN> &sc, con
 
 // Class total of the nonzero patterns in double-float: prod_e (1 + y t_e) as
 // (even part - 1, odd part), lanes own ranks lane*NPL .. lane*NPL+NPL-1, then
-// a butterfly over the warp; lane 0's result is broadcast.
+// a butterfly over the warp; lane 0's result is broadcast.  Every term is
+// nonnegative, so the additions need no cancellation handling.
 template <int NPL, class SYN>
 __device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, int cls, int lane) {
   DF u = {0.f, 0.f}, b = {0.f, 0.f};
@@ -642,8 +655,8 @@ __device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, in
     const int e = lane * NPL + k;
     if (e < n) {
       const float t = sc.hr[e].t;
-      const DF nu = df_add(u, df_mul_f(b, t));
-      const DF nb = df_add(df_add(b, DF{t, 0.f}), df_mul_f(u, t));
+      const DF nu = df_add_pos(u, df_mul_f(b, t));
+      const DF nb = df_add_pos(df_add_pos(b, DF{t, 0.f}), df_mul_f(u, t));
       u = nu;
       b = nb;
     }
@@ -652,12 +665,12 @@ __device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, in
   for (int d = 16; d > 0; d >>= 1) {
     const DF ou = {__shfl_xor_sync(FULL, u.h, d), __shfl_xor_sync(FULL, u.l, d)};
     const DF ob = {__shfl_xor_sync(FULL, b.h, d), __shfl_xor_sync(FULL, b.l, d)};
-    const DF nu = df_add(df_add(u, ou), df_add(df_mul(u, ou), df_mul(b, ob)));
-    const DF nb = df_add(df_add(b, ob), df_add(df_mul(u, ob), df_mul(b, ou)));
+    const DF nu = df_add_pos(df_add_pos(u, ou), df_add_pos(df_mul(u, ou), df_mul(b, ob)));
+    const DF nb = df_add_pos(df_add_pos(b, ob), df_add_pos(df_mul(u, ob), df_mul(b, ou)));
     u = nu;
     b = nb;
   }
-  const DF E = cls == 0 ? u : (cls == 1 ? b : df_add(u, b));
+  const DF E = cls == 0 ? u : (cls == 1 ? b : df_add_pos(u, b));
   return {__shfl_sync(FULL, E.h, 0), __shfl_sync(FULL, E.l, 0)};
 }
 
@@ -1048,7 +1061,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
       const float x = lam[k];
       // sigma(x) and sigma(-x) without cancellation
       const float ex = expf(-fabsf(x));
-      const float sp = 1.f / (1.f + ex), sn = ex * sp;  // sigma(|x|), sigma(-|x|)
+      const float sp = __frcp_rn(1.f + ex), sn = ex * sp;  // sigma(|x|), sigma(-|x|)
       float a0 = pm * (x >= 0.f ? sp : sn);              // miss term, bit 0
       float a1 = pm * (x >= 0.f ? sn : sp);              // miss term, bit 1
       const uint64_t bitm = 1ull << (i & 63);
@@ -1058,7 +1071,8 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
         else
           a0 += sc.wl[l];
       }
-      lapp[k] = (a0 > 1e-30f && a1 > 1e-30f) ? logf(a0 / a1) : lapp_logdomain<NPL, SYN>(sc, nhit, M, x, i);
+      // both sums lie in (1e-30, 1 + 1e-6]: __fdividef's range, 2 ulp
+      lapp[k] = (a0 > 1e-30f && a1 > 1e-30f) ? logf(__fdividef(a0, a1)) : lapp_logdomain<NPL, SYN>(sc, nhit, M, x, i);
     }
   }
 #ifdef SG_PHASE_PROFILE
