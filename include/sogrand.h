@@ -269,6 +269,19 @@ int sogrand_trace_patterns(sogrand_code *code, const float *llr, int64_t max_q, 
  */
 int sogrand_release_cached(void);
 
+/*
+ * Integer-pipe throughput of the current device: 32-bit LOP3 (three-input
+ * logic) and IADD instructions retired per second by every SM at full
+ * occupancy, from a timed kernel of independent dependency chains
+ * (trips x 128 such instructions per thread).  The decoders' ceiling: their
+ * work is integer and logic instructions.  Synchronous on `stream`.
+ *   trips      loop trips, 1 .. 2^30 (about 1.5e5 runs for tens of ms)
+ *   ops_per_s  HOST out: lane-operations per second
+ *   ms_out     HOST out (may be NULL): the timed kernel's duration
+ * Errors: EINVAL, ECUDA.
+ */
+int sogrand_int_peak(int64_t trips, double *ops_per_s, double *ms_out, void *stream);
+
 /* Static text for an error code. */
 const char *sogrand_strerror(int err);
 

@@ -59,11 +59,12 @@ def load() -> C.CDLL:
                                                 C.POINTER(ProductStats), vp]
         L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.sogrand_release_cached.argtypes = []
+        L.sogrand_int_peak.argtypes = [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
-                     "sogrand_trace_patterns", "sogrand_release_cached"):
+                     "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -220,6 +221,13 @@ def product_decode_host(code: Code, llr_ch: np.ndarray, L: int = 4, query_cap: i
 def sogrand_release_cached():
     """Return the idle memory of the library's device pools (call after synchronising)."""
     _check(load().sogrand_release_cached(), "sogrand_release_cached")
+
+
+def sogrand_int_peak(trips: int = 150_000, stream=None):
+    """Measured integer-pipe rate of the current device: (lane-ops/s, kernel ms)."""
+    ops, ms = C.c_double(0), C.c_double(0)
+    _check(load().sogrand_int_peak(int(trips), C.byref(ops), C.byref(ms), _stream(stream)), "sogrand_int_peak")
+    return ops.value, ms.value
 
 
 def unpack_bits(bits, n: int):

@@ -73,7 +73,8 @@ struct SubsetCounts {
 
 // Append, in lexicographic order of the ascending rank vector, every subset
 // of {lo..n} with `left` more elements and sum `rest` (ranks 1-based here,
-// stored 0-based in bytes 1..w of the entry).
+// stored 0-based in bytes 1..w of the entry; bytes past w hold n, the index
+// of a neutral rank record: H column 0, mass factor 1).
 void emit_subsets(int n, int w, int depth, int lo, int64_t rest, uint8_t *bytes, std::vector<uint4> &out) {
   const int left = w - depth;
   if (left == 0) {
@@ -92,7 +93,7 @@ void emit_subsets(int n, int w, int depth, int lo, int64_t rest, uint8_t *bytes,
     bytes[1 + depth] = (uint8_t)(r - 1);
     emit_subsets(n, w, depth + 1, r + 1, rem, bytes, out);
   }
-  bytes[1 + depth] = 0;
+  bytes[1 + depth] = (uint8_t)n;
 }
 
 int build_tables(int n, int64_t cap, int c_max, bool even, HostTables &T) {
@@ -123,7 +124,8 @@ int build_tables(int n, int64_t cap, int c_max, bool even, HostTables &T) {
   for (int w = 0; w < wtop; w++) {
     const int mlo = w * (w + 1) / 2, mhi = w * (2 * n - w + 1) / 2;
     int64_t off = 0;
-    uint8_t bytes[16] = {0};
+    uint8_t bytes[16];
+    std::memset(bytes, n, sizeof(bytes));
     bytes[0] = (uint8_t)w;
     for (int m = mlo; m <= mhi && off <= cap; m++) {
       const int64_t cnt = N.at(w, m);

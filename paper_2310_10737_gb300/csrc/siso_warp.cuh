@@ -197,8 +197,8 @@ struct Layout {
   static constexpr int NM = (NT + 63) / 64;
   static constexpr int o_l2 = 0;                                      // float[NT] |lambda| log2(e), by rank
   static constexpr int o_al = o_l2 + 4 * NT;                          // float[NT] |lambda|, by rank
-  static constexpr int o_hr = o_al + 4 * NT;                          // RankRec[NT] H column + mass factor, by rank
-  static constexpr int o_cw = align16(o_hr + (int)sizeof(RankRec<SYN>) * NT);  // u64[LMAX][NM] listed codewords
+  static constexpr int o_hr = o_al + 4 * NT;  // RankRec[NT + 1] H column + mass factor, by rank; [n] neutral
+  static constexpr int o_cw = align16(o_hr + (int)sizeof(RankRec<SYN>) * (NT + 1));  // u64[LMAX][NM] listed codewords
   static constexpr int o_lp = o_cw + 8 * LMAX * NM;                   // float[LMAX] log p(z)/p(0)
   static constexpr int o_wl = o_lp + 4 * LMAX;                        // float[LMAX] APP of each listed word
   static constexpr int o_perm = o_wl + 4 * LMAX;                      // u8[NT] rank -> bit
@@ -322,8 +322,9 @@ __device__ __forceinline__ int ent_rank(const uint4 &e) {
 
 // XOR of the rank-ordered H columns of a pattern and its mass relative to
 // p(0), the product of its ranks' factors, in double-float (0 for the zero
-// pattern).  The loop runs to the warp's largest weight; shorter patterns
-// mask the extra terms.
+// pattern).  The loop runs to the warp's largest weight; a shorter pattern's
+// extra bytes name the neutral record hr[n] (H column 0, factor 1: the XOR
+// and the products are exact no-ops).
 template <class SYN>
 __device__ __forceinline__ SYN ent_syndrome(const uint4 &e, int w, int wmax, const RankRec<SYN> *hr, DF &mass) {
   SYN s = 0;
@@ -331,11 +332,9 @@ __device__ __forceinline__ SYN ent_syndrome(const uint4 &e, int w, int wmax, con
 #define SG_R(K)                                    \
   if (K < wmax) {                                  \
     const RankRec<SYN> v = hr[ent_rank<K>(e)];     \
-    const bool on = K < w;                         \
-    s ^= on ? v.h : (SYN)0;                        \
-    const float t = on ? v.t : 1.f;                \
-    const float p = __fmul_rn(mh, t);              \
-    ml = fmaf(ml, t, fmaf(mh, t, -p));             \
+    s ^= v.h;                                      \
+    const float p = __fmul_rn(mh, v.t);            \
+    ml = fmaf(ml, v.t, fmaf(mh, v.t, -p));         \
     mh = p;                                        \
   }
   SG_R(0) SG_R(1) SG_R(2) SG_R(3) SG_R(4) SG_R(5) SG_R(6) SG_R(7)
@@ -821,9 +820,12 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
       sxy += qa * (e + 1);
     }
   }
-  sy = warp_sum_i64(sy);
-  sxy = warp_sum_i64(sxy);
+  // sy < 2^27 fits one 32-bit reduction; sxy < 2^34 is split at bit 24
+  sy = (int64_t)__reduce_add_sync(FULL, (unsigned)sy);
+  sxy = ((int64_t)__reduce_add_sync(FULL, (unsigned)(sxy >> 24)) << 24) +
+        (int64_t)__reduce_add_sync(FULL, (unsigned)(sxy & 0xffffff));
   h.c = one_line_c(sy, sxy, n, code.c_max);
+  if (lane == 0) sc.hr[n] = RankRec<SYN>{(SYN)0, 1.f};  // neutral record for unused entry bytes
   __syncwarp();
   return true;
 }
@@ -1047,8 +1049,12 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     res.pmiss = 1.f;
     res.logD = M;
   } else {
-    float D = M;
-    for (int l = 0; l < nhit; l++) D = lse(D, sc.lp[l]);
+    // log(R phi + sum_l p_l), all relative to p(0): max plus log of a sum
+    float mx = M;
+    for (int l = 0; l < nhit; l++) mx = fmaxf(mx, sc.lp[l]);
+    float sum = M == -CUDART_INF_F ? 0.f : expf(M - mx);
+    for (int l = 0; l < nhit; l++) sum += expf(sc.lp[l] - mx);
+    const float D = mx + logf(sum);
     res.logD = D;
     const float pm = M == -CUDART_INF_F ? 0.f : expf(M - D);
     res.pmiss = pm;
