@@ -247,6 +247,9 @@ def main():
     d_in = host.to(dev)
     c = sg.Code.from_linear_code(code)
     log("inputs resident on the device, code tables built")
+    # schedule autotuner (set-up, outside the timed region): blocks per SM on a 10,000-frame sample
+    sched, sched_ms = c.tune(d_in[: min(F, 10_000)], L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER)
+    log(f"schedule: {sched} blocks/SM (sample ms at 6 / 8: {sched_ms[0]:.1f} / {sched_ms[1]:.1f})")
     n, k = code.n, code.k
     out = dict(bits=torch.empty((F, n * n // 8), dtype=torch.uint8, device=dev),
                half_iters=torch.empty(F, dtype=torch.int32, device=dev),
@@ -378,6 +381,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "queries_per_s": world * qtot / (ms / 1000), "xf_words": int(out["xf_words"].item()),
                 "quality": quality,
+                "schedule": {"blocks_per_sm": sched, "tuned_on": f"{min(F, 10_000)} frames",
+                             "sample_ms": {"6": sched_ms[0], "8": sched_ms[1]}},
                 "form": ("persistent (one kernel per decode, device-side frame queue)" if main_persistent
                          else "plain (one launch per half iteration)")}
         if other is not None:

@@ -190,6 +190,65 @@ int product_decode_persistent(sogrand_code *row_code, const sogrand_code *col_co
                               product_decode_stats *stats, void *stream);
 
 /*
+ * Schedule of a code's decoding kernels: the number of resident blocks per SM
+ * (128 threads each) they are compiled for, 6 (80 registers a thread) or 8
+ * (64 registers).  Which is faster depends on the code (register pressure of
+ * its syndrome width and list) and is measured by sogrand_code_tune.  The
+ * default until tuned: 8 for n <= 64 and n - k <= 8, else 6.
+ *   minb     0 (query only), 6 or 8
+ *   current  HOST out (may be NULL): the schedule in force
+ * Not to be changed while a decode of this code is in flight.  Errors: EINVAL.
+ */
+int sogrand_code_schedule(sogrand_code *code, int minb, int *current);
+
+/*
+ * Autotuner: decodes a sample of frames (device [n_frames][n][n] LLRs, with
+ * the decode parameters of the intended workload) with the batched form
+ * under each schedule, twice each (the first run warms caches), and keeps the
+ * faster for this code.  Synchronous on `stream`; writes no caller buffer
+ * but `chosen` (HOST, may be NULL: 6 or 8) and ms_out (HOST [2] or NULL: the
+ * timed runs for 6 and 8 blocks per SM).  Errors: as
+ * product_decode_persistent; EINVAL also for n_frames < 1.
+ */
+int sogrand_code_tune(sogrand_code *code, int64_t n_frames, const float *llr_ch, int L, int64_t query_cap, float thr,
+                      float alpha, int max_iter, int *chosen, float *ms_out, void *stream);
+
+/*
+ * One group of frames of the mixed form: square product frames of one code.
+ * All pointers are device memory of the current device.
+ */
+#define SOGRAND_MIX_MAX_GROUPS 16
+typedef struct {
+  sogrand_code *code;   /* row and column code of the group's frames */
+  int64_t n_frames;     /* >= 0 */
+  const float *llr_ch;  /* [n_frames][n][n] channel LLRs, row-major */
+  uint8_t *bits;        /* [n_frames][ceil(n*n/8)] out (required when n_frames > 0) */
+  int32_t *half_iters;  /* [n_frames] out, or NULL */
+  uint8_t *status;      /* [n_frames] out, or NULL */
+  int64_t *queries;     /* [n_frames] out, or NULL */
+} sogrand_frame_group;
+
+/*
+ * Mixed form of product decoding (Sec. VI turbo decoding of each frame, as
+ * product_decode_persistent): frames of up to SOGRAND_MIX_MAX_GROUPS codes of
+ * different lengths decoded by ONE persistent launch that shares one
+ * frame-half list, so the SMs stay busy across codes (the paper decodes one
+ * code at a time; this is a batching form of the same computation).  Every
+ * frame's results equal those of product_decode_persistent on that frame
+ * alone.  L, query_cap, thr, alpha and max_iter apply to every group.
+ *   groups   HOST [n_groups] (read during the call)
+ *   stats    optional: weight_sum, xf_words, timing_ms[0] (the launch),
+ *            launches (par_queries is ignored)
+ * Synchronous on `stream` (reads the kernel's status).  Errors: EINVAL (as
+ * product_decode_persistent for any group, n_groups outside
+ * 1..SOGRAND_MIX_MAX_GROUPS, total frames x 2 max_iter x 128 >= 2^31),
+ * EUNSUPPORTED (groups whose codes need different syndrome widths: n - k <= 32
+ * and n - k > 32 in one call), ENOMEM, ECUDA, ETIMEOUT.
+ */
+int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L, int64_t query_cap, float thr,
+                         float alpha, int max_iter, product_decode_stats *stats, void *stream);
+
+/*
  * product_decode on HOST buffers: copies llr_ch to the device, decodes with
  * the batched form (product_decode_persistent) and copies the results back
  * before returning.  Batches of 4096 frames or more are split into up to 8

@@ -34,6 +34,12 @@ class SograndError(RuntimeError):
         super().__init__(f"{where}: {strerror(code)} ({code})")
 
 
+class FrameGroup(C.Structure):
+    """sogrand_frame_group: one code's frames in a mixed launch."""
+    _fields_ = [("code", C.c_void_p), ("n_frames", C.c_int64), ("llr_ch", C.c_void_p), ("bits", C.c_void_p),
+                ("half_iters", C.c_void_p), ("status", C.c_void_p), ("queries", C.c_void_p)]
+
+
 def load() -> C.CDLL:
     """Load libsogrand.so; raises if it has not been built."""
     global _lib
@@ -59,12 +65,18 @@ def load() -> C.CDLL:
                                                 C.POINTER(ProductStats), vp]
         L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.sogrand_release_cached.argtypes = []
+        L.sogrand_code_schedule.argtypes = [vp, i32, C.POINTER(C.c_int)]
+        L.sogrand_code_tune.argtypes = [vp, i64, vp, i32, i64, f32, f32, i32, C.POINTER(C.c_int),
+                                        C.POINTER(C.c_float), vp]
+        L.product_decode_mixed.argtypes = [i32, C.POINTER(FrameGroup), i32, i64, f32, f32, i32,
+                                           C.POINTER(ProductStats), vp]
         L.sogrand_int_peak.argtypes = [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
-                     "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak"):
+                     "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak",
+                     "product_decode_mixed", "sogrand_code_schedule", "sogrand_code_tune"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -117,6 +129,22 @@ class Code:
 
     def reserve(self, max_query_cap: int):
         _check(load().sogrand_code_reserve(self._h, int(max_query_cap)), "sogrand_code_reserve")
+
+    def schedule(self, minb: int = 0) -> int:
+        """Set (6 or 8) or query (0) the blocks per SM the decoding kernels run at."""
+        cur = C.c_int(0)
+        _check(load().sogrand_code_schedule(self.handle, int(minb), C.byref(cur)), "sogrand_code_schedule")
+        return cur.value
+
+    def tune(self, llr_sample, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
+             max_iter: int = 20, stream=None):
+        """Autotune the schedule on a device sample [F, n, n]; returns (chosen, (ms at 6, ms at 8))."""
+        ch = C.c_int(0)
+        ms = (C.c_float * 2)()
+        _check(load().sogrand_code_tune(self.handle, int(llr_sample.shape[0]), _ptr(llr_sample), int(L),
+                                        int(query_cap), float(thr), float(alpha), int(max_iter), C.byref(ch),
+                                        C.cast(ms, C.POINTER(C.c_float)), _stream(stream)), "sogrand_code_tune")
+        return ch.value, (float(ms[0]), float(ms[1]))
 
     def close(self):
         if getattr(self, "_h", None):
@@ -196,6 +224,42 @@ def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: 
         out["timing_ms"] = (float(tm[0]), float(tm[1]))
         out["launches"] = int(ln[0])
     return out
+
+
+def product_decode_mixed(groups, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
+                         max_iter: int = 20, stream=None, stats: bool = True):
+    """Frames of several codes in one launch.  groups: list of (Code, llr [F, n, n] float32 CUDA tensor).
+    Returns (list of per-group output dicts of CUDA tensors, info dict)."""
+    import torch
+    outs, arr = [], (FrameGroup * len(groups))()
+    for g, (code, llr) in enumerate(groups):
+        F, n, n2 = llr.shape
+        assert n == n2 == code.n and llr.is_cuda and llr.dtype == torch.float32 and llr.is_contiguous()
+        dev = llr.device
+        o = dict(bits=torch.empty((F, (n * n + 7) // 8), dtype=torch.uint8, device=dev),
+                 half_iters=torch.empty(F, dtype=torch.int32, device=dev),
+                 status=torch.empty(F, dtype=torch.uint8, device=dev),
+                 queries=torch.empty(F, dtype=torch.int64, device=dev))
+        outs.append(o)
+        arr[g] = FrameGroup(code.handle, F, _ptr(llr), _ptr(o["bits"]), _ptr(o["half_iters"]), _ptr(o["status"]),
+                            _ptr(o["queries"]))
+    info = {}
+    st = None
+    if stats:
+        dev = groups[0][1].device
+        info["weight_sum"] = torch.zeros(1, dtype=torch.int64, device=dev)
+        info["xf_words"] = torch.zeros(1, dtype=torch.int32, device=dev)
+        tm = (C.c_float * 2)()
+        ln = (C.c_int32 * 1)()
+        st = ProductStats(None, _ptr(info["weight_sum"]), _ptr(info["xf_words"]), C.cast(tm, C.POINTER(C.c_float)),
+                          C.cast(ln, C.POINTER(C.c_int32)))
+    rc = load().product_decode_mixed(len(groups), arr, int(L), int(query_cap), float(thr), float(alpha), int(max_iter),
+                                     C.byref(st) if st is not None else None, _stream(stream))
+    _check(rc, "product_decode_mixed")
+    if stats:
+        info["timing_ms"] = float(tm[0])
+        info["launches"] = int(ln[0])
+    return outs, info
 
 
 def product_decode_host(code: Code, llr_ch: np.ndarray, L: int = 4, query_cap: int = 10**4, thr: float = 0.0,

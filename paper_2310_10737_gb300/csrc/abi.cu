@@ -23,6 +23,7 @@ struct sogrand_code {
   void *d_tab = nullptr;
   sg::DevOrder ord{};
   int jmax = 1;
+  int minb = 6;  // schedule: resident blocks per SM (6 or 8), see sogrand_code_tune
   int64_t tab_cap = 0;
   int64_t tab_bytes = 0;
   std::mutex mu;
@@ -234,6 +235,7 @@ sg::DevCode dev_code(const sogrand_code *c) {
   d.hrow = c->d_hrow;
   d.ord = c->ord;
   d.jmax = c->jmax;
+  d.minb = c->minb;
   return d;
 }
 
@@ -347,10 +349,15 @@ int ensure_cap(sogrand_code *c, int64_t cap) {
 }  // namespace
 
 namespace sg {
-int scratch_bytes(int npl, int syn_bytes, int jmax) {
-  if (npl == 1) return syn_bytes == 4 ? Layout<1, uint32_t>::bytes(jmax) : Layout<1, uint64_t>::bytes(jmax);
-  if (npl == 2) return syn_bytes == 4 ? Layout<2, uint32_t>::bytes(jmax) : Layout<2, uint64_t>::bytes(jmax);
-  return syn_bytes == 4 ? Layout<4, uint32_t>::bytes(jmax) : Layout<4, uint64_t>::bytes(jmax);
+int warp_area_bytes(int npl, int syn_bytes) {
+  if (npl == 1) return syn_bytes == 4 ? Layout<1, uint32_t>::warp_bytes : Layout<1, uint64_t>::warp_bytes;
+  if (npl == 2) return syn_bytes == 4 ? Layout<2, uint32_t>::warp_bytes : Layout<2, uint64_t>::warp_bytes;
+  return syn_bytes == 4 ? Layout<4, uint32_t>::warp_bytes : Layout<4, uint64_t>::warp_bytes;
+}
+int dp_area_bytes(int npl, int syn_bytes, int jmax) {
+  if (npl == 1) return syn_bytes == 4 ? Layout<1, uint32_t>::dp_bytes(jmax) : Layout<1, uint64_t>::dp_bytes(jmax);
+  if (npl == 2) return syn_bytes == 4 ? Layout<2, uint32_t>::dp_bytes(jmax) : Layout<2, uint64_t>::dp_bytes(jmax);
+  return syn_bytes == 4 ? Layout<4, uint32_t>::dp_bytes(jmax) : Layout<4, uint64_t>::dp_bytes(jmax);
 }
 }  // namespace sg
 
@@ -392,6 +399,9 @@ int sogrand_code_create(int n, int k, const uint8_t *H, int even, sogrand_code *
   c->even = even;
   c->c_max = n;
   c->nm = (n + 63) / 64;
+  // default schedule until tuned: 8 blocks per SM (64 registers) for short
+  // codes with few checks, else 6 (80 registers)
+  c->minb = (n <= 64 && m <= 8) ? 8 : 6;
   c->log_phi = (float)(log_pow2m1(k) - log_pow2m1(even ? n - 1 : n));
   cudaGetDevice(&c->device);
   std::vector<uint64_t> hcol(n, 0), hrow((size_t)m * c->nm, 0);
@@ -681,6 +691,54 @@ int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_
   return err ? SOGRAND_ETIMEOUT : SOGRAND_OK;
 }
 
+int sogrand_code_schedule(sogrand_code *c, int minb, int *current) {
+  if (!c || (minb != 0 && minb != 6 && minb != 8)) return SOGRAND_EINVAL;
+  if (minb) c->minb = minb;
+  if (current) *current = c->minb;
+  return SOGRAND_OK;
+}
+
+int sogrand_code_tune(sogrand_code *c, int64_t F, const float *llr_ch, int L, int64_t cap, float thr, float alpha,
+                      int max_iter, int *chosen, float *ms_out, void *stream) {
+  int rc = persistent_check(c, c, F, L, cap, thr, alpha, max_iter);
+  if (rc != SOGRAND_OK) return rc;
+  if (F < 1 || !llr_ch) return SOGRAND_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nb = ((size_t)c->n * c->n + 7) / 8;
+  char *bits = nullptr;
+  if (scratch_alloc(&bits, al256((size_t)F * nb), s) != cudaSuccess) return SOGRAND_ENOMEM;
+  const int cand[2] = {6, 8};
+  float best = 0.f, ms[2] = {0.f, 0.f};
+  int pick = c->minb;
+  const int keep = c->minb;
+  for (int i = 0; i < 2 && rc == SOGRAND_OK; i++) {
+    c->minb = cand[i];
+    float t = 0.f;
+    for (int rep = 0; rep < 2 && rc == SOGRAND_OK; rep++) {  // the first run warms caches and the pool
+      float tm[2] = {0.f, 0.f};
+      product_decode_stats st{nullptr, nullptr, nullptr, tm, nullptr};
+      rc = product_decode_persistent(c, c, F, llr_ch, L, cap, thr, alpha, max_iter, (uint8_t *)bits, nullptr,
+                                     nullptr, nullptr, &st, stream);
+      t = tm[0];
+    }
+    ms[i] = t;
+    if (rc == SOGRAND_OK && (i == 0 || t < best)) {
+      best = t;
+      pick = cand[i];
+    }
+  }
+  c->minb = rc == SOGRAND_OK ? pick : keep;
+  if (cudaFreeAsync(bits, s) != cudaSuccess && rc == SOGRAND_OK) rc = SOGRAND_ECUDA;
+  if (rc == SOGRAND_OK) {
+    if (chosen) *chosen = pick;
+    if (ms_out) {
+      ms_out[0] = ms[0];
+      ms_out[1] = ms[1];
+    }
+  }
+  return rc;
+}
+
 int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
                         int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
                         uint8_t *status, int64_t *queries, void *stream) {
@@ -768,6 +826,133 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   for (int k = 0; k < 8; k++)
     if (err[k]) return SOGRAND_ETIMEOUT;
   return SOGRAND_OK;
+}
+
+int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L, int64_t cap, float thr, float alpha,
+                         int max_iter, product_decode_stats *stats, void *stream) {
+  if (stats && stats->timing_ms) stats->timing_ms[0] = stats->timing_ms[1] = 0.f;
+  if (stats && stats->launches) stats->launches[0] = 0;
+  static_assert(SOGRAND_MIX_MAX_GROUPS == sg::MIX_MAX_GROUPS, "group table size");
+  if (n_groups < 1 || n_groups > SOGRAND_MIX_MAX_GROUPS || !groups) return SOGRAND_EINVAL;
+  int64_t total = 0;
+  int slot_n = 0, syn64 = -1;
+  for (int g = 0; g < n_groups; g++) {
+    const sogrand_frame_group &G = groups[g];
+    int rc = persistent_check(G.code, G.code, G.n_frames, L, cap, thr, alpha, max_iter);
+    if (rc != SOGRAND_OK) return rc;
+    if (G.n_frames > 0 && (!G.llr_ch || !G.bits)) return SOGRAND_EINVAL;
+    const int s64 = G.code->m > 32 ? 1 : 0;
+    if (syn64 >= 0 && s64 != syn64) return SOGRAND_EUNSUPPORTED;  // one syndrome width per launch
+    syn64 = s64;
+    total += G.n_frames;
+    slot_n = std::max(slot_n, G.code->n);
+  }
+  if (total * 2 * (int64_t)max_iter * 128 >= (int64_t(1) << 31) - (int64_t(1) << 22)) return SOGRAND_EINVAL;
+  if (total == 0) return SOGRAND_OK;
+  for (int g = 0; g < n_groups; g++) {
+    int rc = ensure_cap(groups[g].code, cap);
+    if (rc != SOGRAND_OK) return rc;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int max_half = 2 * max_iter;
+  // scratch: per group the persistent-form buffers, then the shared list,
+  // the control words and the device copy of the group table
+  std::vector<size_t> off(n_groups);
+  size_t bytes = 0;
+  for (int g = 0; g < n_groups; g++) {
+    off[g] = bytes;
+    bytes += al256(persistent_scratch_bytes(groups[g].n_frames, groups[g].code->n, groups[g].code->nm, max_iter));
+  }
+  const size_t o_queue = bytes, o_ctrl = o_queue + al256((size_t)total * max_half * sizeof(int32_t));
+  const size_t o_tab = o_ctrl + 256, total_bytes = o_tab + al256(n_groups * sizeof(sg::MixGroup));
+  char *mem = nullptr;
+  if (scratch_alloc(&mem, total_bytes, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  sg::MixGroup tab[SOGRAND_MIX_MAX_GROUPS] = {};
+  int wstride = 0, dpbytes = 0;
+  int64_t first = 0;
+  for (int g = 0; g < n_groups; g++) {
+    const sogrand_frame_group &G = groups[g];
+    sogrand_code *c = G.code;
+    const int npl = c->n <= 32 ? 1 : (c->n <= 64 ? 2 : 4);
+    wstride = std::max(wstride, sg::warp_area_bytes(npl, syn64 ? 8 : 4));
+    dpbytes = std::max(dpbytes, sg::dp_area_bytes(npl, syn64 ? 8 : 4, c->jmax));
+    char *p = mem + off[g];
+    auto take = [&p](size_t b) {
+      char *r = p;
+      p += al256(b);
+      return r;
+    };
+    const int64_t F = G.n_frames;
+    const size_t b_i32 = (size_t)F * 4, b_i64 = (size_t)F * 8;
+    sg::ProductArgs a{};
+    a.n_frames = F;
+    a.llr_ch = G.llr_ch;
+    a.alpha = alpha;
+    a.max_half = max_half;
+    a.le = (float *)take((size_t)F * c->n * c->n * sizeof(float));
+    a.hb = (uint64_t *)take((size_t)F * c->n * c->nm * sizeof(uint64_t));
+    a.hmax = (int32_t *)take(b_i32);
+    a.half_cur = (int32_t *)take(b_i32);
+    a.done_words = (int32_t *)take(b_i32);
+    a.bad = (int32_t *)take(b_i32);
+    take((size_t)F * 2 * max_iter * sizeof(int32_t));  // (the single-code list, unused here)
+    int32_t *hi_s = (int32_t *)take(b_i32);
+    int64_t *q_s = (int64_t *)take(b_i64);
+    int64_t *pq_s = (int64_t *)take(b_i64);
+    uint8_t *st_s = (uint8_t *)take((size_t)F);
+    a.bits = G.bits;
+    a.half_iters = G.half_iters ? G.half_iters : hi_s;
+    a.queries = G.queries ? G.queries : q_s;
+    a.par_queries = pq_s;
+    a.status = G.status ? G.status : st_s;
+    a.ctrl = (int32_t *)(mem + o_ctrl);  // a lock timeout in a word stops the launch
+    sg::MixGroup &M = tab[g];
+    M.code = dev_code(c);
+    M.P = sg::SisoParams{L, (int32_t)cap, thr};
+    M.a = a;
+    M.frames = nullptr;
+    M.first = first;
+    M.count = F;
+    M.npl = npl;
+    M.fresh = 1;
+    first += F;
+  }
+  sg::MixArgs m{};
+  m.groups = (const sg::MixGroup *)(mem + o_tab);
+  m.ngroups = n_groups;
+  m.total = total;
+  m.slot_n = slot_n;
+  m.max_half = max_half;
+  m.wstride = wstride;
+  m.dpbytes = dpbytes;
+  m.queue = (int32_t *)(mem + o_queue);
+  m.ctrl = (int32_t *)(mem + o_ctrl);
+  m.max_spin = 2000000;
+  m.xf_count = stats ? stats->xf_words : nullptr;
+  m.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
+  const bool timed = stats && stats->timing_ms;
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  cudaError_t e = cudaMemcpyAsync(mem + o_tab, tab, n_groups * sizeof(sg::MixGroup), cudaMemcpyHostToDevice, s);
+  if (timed)
+    for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(ev[0], s);
+  if (e == cudaSuccess)
+    e = syn64 ? sg::launch_product_mixed<uint64_t>(m, tab, 0, s) : sg::launch_product_mixed<uint32_t>(m, tab, 0, s);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(ev[1], s);
+  int32_t err = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, m.ctrl + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && timed) {
+    float x = 0.f;
+    e = cudaEventElapsedTime(&x, ev[0], ev[1]);
+    stats->timing_ms[0] = x;
+  }
+  for (int i = 0; i < 2; i++)
+    if (ev[i]) cudaEventDestroy(ev[i]);
+  if (stats && stats->launches) stats->launches[0] = 2;
+  cudaError_t e2 = cudaFreeAsync(mem, s);
+  if (e != cudaSuccess || e2 != cudaSuccess) return SOGRAND_ECUDA;
+  return err ? SOGRAND_ETIMEOUT : SOGRAND_OK;
 }
 
 int product_decode(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch, int L,

@@ -21,20 +21,36 @@ namespace sg {
 
 constexpr int TPB = 32 * WARPS_PER_BLOCK;
 
+// dynamic shared memory of one block of a single-code kernel
 template <int NPL, class SYN>
-__host__ __device__ inline int warp_scratch_bytes(int jmax) {
-  return Layout<NPL, SYN>::bytes(jmax);
+__host__ __device__ inline int block_scratch_bytes(int jmax) {
+  return Layout<NPL, SYN>::block_bytes(jmax);
+}
+
+// Bind warp `warp`'s view of the block's shared memory (per-warp areas of
+// `wstride` bytes, then the remaining-mass area of `dpbytes` and its lock).
+template <int NPL, class SYN>
+__device__ __forceinline__ void bind_scratch(Scratch<NPL, SYN> &sc, unsigned char *smem, int warp, int wstride,
+                                             int dpbytes) {
+  sc.bind(smem + warp * wstride, smem + WARPS_PER_BLOCK * wstride, dpbytes);
+}
+
+// Clear the block's remaining-mass lock (every thread of the block calls this).
+__device__ __forceinline__ void init_block_lock(unsigned char *smem, int wstride, int dpbytes) {
+  if (threadIdx.x == 0) *reinterpret_cast<int *>(smem + WARPS_PER_BLOCK * wstride + dpbytes) = 0;
+  __syncthreads();
 }
 
 // ---------------------------------------------------------------------------
-template <int NPL, class SYN>
-__global__ void __launch_bounds__(TPB, 6) k_decode(const DevCode code, const SisoParams P, const DecodeArgs a,
-                                                int wbytes) {
+template <int NPL, class SYN, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const SisoParams P, const DecodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  using LY = Layout<NPL, SYN>;
   constexpr int NM = (32 * NPL + 63) / 64;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
   Scratch<NPL, SYN> sc;
-  sc.bind(smem + warp * wbytes);
+  bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(code.jmax));
   const int n = code.n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   for (int64_t w = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp; w < a.n_words; w += nwarps) {
@@ -68,7 +84,7 @@ __global__ void __launch_bounds__(TPB, 6) k_decode(const DevCode code, const Sis
       if (a.p_miss) a.p_miss[w] = res.pmiss;
       if (a.queries) a.queries[w] = res.queries;
       if (a.list_count) a.list_count[w] = res.nhit;
-      if (used_xf && a.xf_count) atomicAdd(a.xf_count, 1);
+      if ((used_xf & 1) && a.xf_count) atomicAdd(a.xf_count, 1);
       if (a.wsum) atomicAdd(a.wsum, (unsigned long long)res.wsum);
     }
     if (a.list_words || a.list_app) {
@@ -76,8 +92,8 @@ __global__ void __launch_bounds__(TPB, 6) k_decode(const DevCode code, const Sis
         if (a.list_words)
 #pragma unroll
           for (int wd = 0; wd < NM; wd++)
-            a.list_words[((size_t)w * P.L + l) * NM + wd] = l < res.nhit ? sc.cw[l * NM + wd] : 0ull;
-        if (a.list_app) a.list_app[(size_t)w * P.L + l] = l < res.nhit ? sc.wl[l] : 0.f;
+            a.list_words[((size_t)w * P.L + l) * NM + wd] = l < res.nhit ? sc.cw()[l * NM + wd] : 0ull;
+        if (a.list_app) a.list_app[(size_t)w * P.L + l] = l < res.nhit ? sc.wl()[l] : 0.f;
       }
     }
     __syncwarp();
@@ -86,11 +102,13 @@ __global__ void __launch_bounds__(TPB, 6) k_decode(const DevCode code, const Sis
 
 template <int NPL, class SYN>
 __global__ void k_trace(const DevCode code, const float *lam_in, int max_q, uint64_t *out, int32_t *count,
-                        int32_t *c_out, int wbytes) {
+                        int32_t *c_out) {
   extern __shared__ __align__(16) unsigned char smem[];
+  using LY = Layout<NPL, SYN>;
   const int lane = threadIdx.x & 31;
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
   Scratch<NPL, SYN> sc;
-  sc.bind(smem);
+  bind_scratch(sc, smem, 0, LY::warp_bytes, LY::dp_bytes(code.jmax));
   float lam[NPL];
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
@@ -185,7 +203,8 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
       atomicMax(a.hmax + f, res.queries);
       tally.wsum += (unsigned long long)res.wsum;
     }
-    tally.xf += used_xf;
+    tally.xf += used_xf & 1;
+    if ((used_xf & 2) && a.ctrl) atomicExch(a.ctrl + 3, 2);  // stops a persistent launch: reported as a timeout
   }
   __syncwarp();
 #ifdef SG_PHASE_PROFILE
@@ -243,35 +262,14 @@ __device__ __forceinline__ bool frame_valid(const DevCode &code, const uint64_t 
   return ok;
 }
 
-// Write the frame's decision as row-major bits and its status.  R is scratch
-// for the row words (n * NM).
+// Write the frame's decision as row-major bits and its status.  W holds the
+// words of the last half: rows (bit j of word i is bit (i, j)) or columns
+// (bit i of word j is bit (i, j)).
 template <int NPL>
 __device__ __forceinline__ void frame_finish(const DevCode &code, const ProductArgs &a, int64_t f, bool rows,
-                                             int half, int status, const uint64_t *W, uint64_t *R, int lane) {
+                                             int half, int status, const uint64_t *W, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
   const int n = code.n;
-  const uint64_t *src = W;
-  if (!rows) {
-#pragma unroll
-    for (int k = 0; k < NPL; k++) {
-      const int i = lane + 32 * k;
-      if (i < n) {
-        uint64_t r[NM];
-#pragma unroll
-        for (int x = 0; x < NM; x++) r[x] = 0;
-        for (int j = 0; j < n; j++) {
-          const uint64_t bit = (W[j * NM + (i >> 6)] >> (i & 63)) & 1ull;
-#pragma unroll
-          for (int x = 0; x < NM; x++)
-            if ((j >> 6) == x) r[x] |= bit << (j & 63);
-        }
-#pragma unroll
-        for (int x = 0; x < NM; x++) R[i * NM + x] = r[x];
-      }
-    }
-    __syncwarp();
-    src = R;
-  }
   const int nbytes = (n * n + 7) / 8;
   uint8_t *out = a.bits + (size_t)f * nbytes;
   for (int by = lane; by < nbytes; by += 32) {
@@ -281,7 +279,8 @@ __device__ __forceinline__ void frame_finish(const DevCode &code, const ProductA
       const int p = by * 8 + t;
       if (p < n * n) {
         const int i = p / n, j = p - i * n;
-        v |= (unsigned)((src[i * NM + (j >> 6)] >> (j & 63)) & 1ull) << t;
+        const uint64_t word = rows ? W[i * NM + (j >> 6)] >> (j & 63) : W[j * NM + (i >> 6)] >> (i & 63);
+        v |= (unsigned)(word & 1ull) << t;
       }
     }
     out[by] = (uint8_t)v;
@@ -294,13 +293,15 @@ __device__ __forceinline__ void frame_finish(const DevCode &code, const ProductA
 }
 
 // ---- plain form: one launch per half iteration, then a check launch ----
-template <int NPL, class SYN, bool ROWS>
-__global__ void __launch_bounds__(TPB, 6) k_product_half(const DevCode code, const SisoParams P, const ProductArgs a,
-                                                      int half, int wbytes) {
+template <int NPL, class SYN, bool ROWS, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode code, const SisoParams P, const ProductArgs a,
+                                                      int half) {
   extern __shared__ __align__(16) unsigned char smem[];
+  using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
   Scratch<NPL, SYN> sc;
-  sc.bind(smem + warp * wbytes);
+  bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(code.jmax));
   const int n = code.n;
   const int64_t items = a.n_frames * n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
@@ -323,7 +324,6 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode code, const
   constexpr int NM = (32 * NPL + 63) / 64;
   constexpr int NT = 32 * NPL;
   __shared__ uint64_t words_s[WARPS_PER_BLOCK][NT * NM];
-  __shared__ uint64_t rows_s[WARPS_PER_BLOCK][NT * NM];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int n = code.n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
@@ -346,13 +346,106 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode code, const
       __syncwarp();
       continue;
     }
-    frame_finish<NPL>(code, a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, rows_s[warp], lane);
+    frame_finish<NPL>(code, a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, lane);
     if (lane == 0) a.fstate[f] = bad ? F_BAD : (ok ? F_DECODED : F_MAXIT);
     __syncwarp();
   }
 }
 
-// ---- persistent form: one launch decodes the whole batch ----
+// ---- persistent forms: one launch decodes the whole batch ----
+
+// Draw a word ticket and wait until its slot of the frame-half list is
+// filled.  Returns 1 with *f1 = frame + 1 (list entry), or 0 when the launch
+// is over (every frame finished or parked, or the error flag is set).  The
+// wait backs off exponentially and gives up after max_spin microseconds of
+// sleep, setting the error flag.  All reads of shared state are made by lane 0
+// and broadcast, so the whole warp takes the same branch.
+__device__ __forceinline__ int sched_take(int32_t *ctrl_w, const volatile int32_t *queue, int64_t nslots,
+                                          int64_t frames, int slot_n, int max_spin, int lane, int *slot_out,
+                                          int *word_out, int *f1_out) {
+  volatile int32_t *ctrl = ctrl_w;  // [0] slots reserved, [1] word tickets, [2] finished frames, [3] error
+  int ticket = 0;
+  if (lane == 0) ticket = atomicAdd(ctrl_w + 1, 1);
+  ticket = __shfl_sync(FULL, ticket, 0);
+  const int slot = ticket / slot_n;
+  int f1 = 0, st = 0;  // st: 0 wait, 1 work, 2 stop
+  long long slept = 0;
+  unsigned nap = 64;
+  for (;;) {
+    if (lane == 0) {
+      if (ctrl[3] != 0) {
+        st = 2;
+      } else if (slot < nslots && (f1 = queue[slot]) != 0) {
+        st = 1;
+      } else if (ctrl[2] >= frames) {
+        st = 2;  // every frame finished: this ticket has no work
+      } else {
+        st = 0;
+      }
+    }
+    st = __shfl_sync(FULL, st, 0);
+    if (st != 0) break;
+    if (slept > (long long)max_spin * 1000) {
+      if (lane == 0) atomicExch(ctrl_w + 3, 1);
+      st = 2;
+      break;
+    }
+    __nanosleep(nap);
+    slept += nap;
+    if (nap < 8192) nap <<= 1;
+  }
+  if (st == 2) return 0;
+  *slot_out = slot;
+  *word_out = ticket - slot * slot_n;
+  *f1_out = __shfl_sync(FULL, f1, 0);
+  __threadfence();  // acquire: the frame's state for this half
+  return 1;
+}
+
+// After the last word of a half of frame f (list entry f + 1 in the launch's
+// index space `gf`): check the frame and finish it, park it (a serving epoch
+// ran out: its state stays for the next launch) or append its next half.
+template <int NPL>
+__device__ __forceinline__ void frame_after_half(const DevCode &code, const ProductArgs &a, int32_t *ctrl,
+                                                 int32_t *queue_w, int64_t f, int64_t gf, int half, uint64_t *W,
+                                                 int lane) {
+  constexpr int NM = (32 * NPL + 63) / 64;
+  const int n = code.n;
+  __threadfence();
+  const bool rows = (half & 1) != 0;
+  for (int x = lane; x < n * NM; x += 32) W[x] = ld_state<true>(a.hb + (size_t)f * n * NM + x);
+  __syncwarp();
+  const bool ok = frame_valid<NPL>(code, W, lane);
+  int bad = 0, stop = 0;
+  if (lane == 0) {
+    bad = __ldcg(a.bad + f);
+    a.par_queries[f] += __ldcg(a.hmax + f);
+    a.hmax[f] = 0;
+    stop = a.half_stop ? __ldcg(a.half_stop + f) : a.max_half;
+  }
+  bad = __shfl_sync(FULL, bad, 0);
+  stop = __shfl_sync(FULL, stop, 0);
+  if (bad || ok || half >= a.max_half) {
+    frame_finish<NPL>(code, a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, lane);
+    __threadfence();
+    if (lane == 0) atomicAdd(ctrl + 2, 1);
+  } else if (half >= stop) {
+    if (lane == 0) {  // parked: resumes at half + 1 in a later launch
+      a.half_cur[f] = half + 1;
+      a.done_words[f] = 0;
+      __threadfence();
+      atomicAdd(ctrl + 2, 1);
+    }
+  } else if (lane == 0) {
+    a.half_cur[f] = half + 1;
+    a.done_words[f] = 0;
+    __threadfence();
+    const int t = atomicAdd(ctrl + 0, 1);  // < nslots: every frame appends at most max_half - 1 times
+    atomicExch(queue_w + t, (int)(gf + 1));
+  }
+  __syncwarp();
+}
+
 // Frame-halves are appended to a list (a.queue[s] = frame + 1 once slot s is
 // filled); the first F slots hold every frame's first half.  Warps draw
 // global word tickets T: slot T / n, word T mod n, one atomic per word.  The
@@ -361,59 +454,22 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode code, const
 // slot is not filled yet waits with exponential back-off; all waits are
 // bounded (a.max_spin microseconds of accumulated sleep without progress):
 // the kernel then records an error and every warp returns.
-template <int NPL, class SYN>
-__global__ void __launch_bounds__(TPB, 6) k_product_persistent(const DevCode code, const SisoParams P,
-                                                               const ProductArgs a, int wbytes) {
+template <int NPL, class SYN, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode code, const SisoParams P,
+                                                               const ProductArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  constexpr int NM = (32 * NPL + 63) / 64;
-  constexpr int NT = 32 * NPL;
+  using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
   Scratch<NPL, SYN> sc;
-  sc.bind(smem + warp * wbytes);
+  bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(code.jmax));
   const int n = code.n;
-  const int64_t F = a.n_frames;
-  volatile int32_t *ctrl = a.ctrl;  // [0] slots reserved, [1] word tickets, [2] finished frames, [3] error
-  const int64_t nslots = F * (int64_t)a.max_half;  // a frame has at most max_half halves
-  const volatile int32_t *queue = a.queue;
-  uint64_t *W = reinterpret_cast<uint64_t *>(sc.tail);
-  uint64_t *R = W + NT * NM;
-  // Every read of shared scheduling state is made by lane 0 and broadcast, so
-  // the whole warp always takes the same branch.
+  const int64_t nslots = a.n_frames * (int64_t)a.max_half;  // a frame has at most max_half halves
   WarpTally tally;
   for (;;) {
-    int ticket = 0;
-    if (lane == 0) ticket = atomicAdd(a.ctrl + 1, 1);
-    ticket = __shfl_sync(FULL, ticket, 0);
-    const int slot = ticket / n, w = ticket - slot * n;
-    int f1 = 0, st = 0;  // st: 0 wait, 1 work, 2 stop
-    long long slept = 0;
-    unsigned nap = 64;
-    for (;;) {
-      if (lane == 0) {
-        if (ctrl[3] != 0) {
-          st = 2;
-        } else if (slot < nslots && (f1 = queue[slot]) != 0) {
-          st = 1;
-        } else if (ctrl[2] >= F) {
-          st = 2;  // every frame finished: this ticket has no work
-        } else {
-          st = 0;
-        }
-      }
-      st = __shfl_sync(FULL, st, 0);
-      if (st != 0) break;
-      if (slept > (long long)a.max_spin * 1000) {
-        if (lane == 0) atomicExch(a.ctrl + 3, 1);
-        st = 2;
-        break;
-      }
-      __nanosleep(nap);
-      slept += nap;
-      if (nap < 8192) nap <<= 1;
-    }
-    if (st == 2) break;
-    const int64_t f = (int64_t)__shfl_sync(FULL, f1, 0) - 1;
-    __threadfence();  // acquire: the frame's state for this half
+    int slot, w, f1;
+    if (!sched_take(a.ctrl, a.queue, nslots, a.n_frames, n, a.max_spin, lane, &slot, &w, &f1)) break;
+    const int64_t f = (int64_t)f1 - 1;
     int half = 0;
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
@@ -425,33 +481,123 @@ __global__ void __launch_bounds__(TPB, 6) k_product_persistent(const DevCode cod
     if (lane == 0) done = atomicAdd(a.done_words + f, 1);
     done = __shfl_sync(FULL, done, 0);
     if (done != n - 1) continue;
-    // last word of this half: check the frame
-    __threadfence();
-    const bool rows = (half & 1) != 0;
-    for (int x = lane; x < n * NM; x += 32) W[x] = ld_state<true>(a.hb + (size_t)f * n * NM + x);
-    __syncwarp();
-    const bool ok = frame_valid<NPL>(code, W, lane);
-    int bad = 0;
-    if (lane == 0) {
-      bad = __ldcg(a.bad + f);
-      a.par_queries[f] += __ldcg(a.hmax + f);
-      a.hmax[f] = 0;
-    }
-    bad = __shfl_sync(FULL, bad, 0);
-    if (bad || ok || half >= a.max_half) {
-      frame_finish<NPL>(code, a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, R, lane);
-      __threadfence();
-      if (lane == 0) atomicAdd(a.ctrl + 2, 1);
-    } else if (lane == 0) {
-      a.half_cur[f] = half + 1;
-      a.done_words[f] = 0;
-      __threadfence();
-      const int t = atomicAdd(a.ctrl + 0, 1);  // < nslots: every frame appends at most max_half - 1 times
-      atomicExch(a.queue + t, (int)(f + 1));
-    }
-    __syncwarp();
+    frame_after_half<NPL>(code, a, a.ctrl, a.queue, f, f, half, sc.W(), lane);
   }
   tally.flush(a, lane);
+}
+
+// ---- mixed form: frames of several codes (uneven n) in one launch ----
+// Groups of frames, one code each, share one frame-half list and ticket
+// counter.  List entry e (1-based) is frame e - 1 of the launch, i.e. entry
+// li = e - 1 - first of the group whose range holds it, and that group's
+// frame (buffer index) frames[li] (li when frames is null).  Slots hold
+// slot_n = the largest n of the launch word tickets; tickets past a frame's n
+// are skipped.  The SISO and the frame check run the instantiation of the
+// group's lanes-per-bit count NPL.
+template <class SYN, int NPL>
+__device__ __forceinline__ int mixed_word(const MixGroup &G, unsigned char *smem, int warp, int wstride, int dpbytes,
+                                          int64_t f, int w, int half, int lane, WarpTally &tally) {
+  Scratch<NPL, SYN> sc;
+  bind_scratch(sc, smem, warp, wstride, dpbytes);
+  const int q = product_word<NPL, SYN, true>(G.code, G.P, G.a, sc, f, w, half, lane, tally);
+  return q;
+}
+
+template <class SYN>
+__global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // the group table, copied into shared memory after the warps' areas, the
+  // remaining-mass area and its lock
+  MixGroup *tab = reinterpret_cast<MixGroup *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16);
+  {
+    const int words = m.ngroups * (int)(sizeof(MixGroup) / 4);
+    const int *src = reinterpret_cast<const int *>(m.groups);
+    int *dst = reinterpret_cast<int *>(tab);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+  }
+  init_block_lock(smem, m.wstride, m.dpbytes);
+  unsigned char *wsm = smem + warp * m.wstride;
+  const int64_t nslots = m.total * (int64_t)m.max_half;
+  WarpTally tally;
+  for (;;) {
+    int slot, w, f1;
+    if (!sched_take(m.ctrl, m.queue, nslots, m.total, m.slot_n, m.max_spin, lane, &slot, &w, &f1)) break;
+    const int64_t gf = (int64_t)f1 - 1;
+    int g = 0;
+    if (lane == 0)
+      while (g + 1 < m.ngroups && m.groups[g + 1].first <= gf) g++;
+    g = __shfl_sync(FULL, g, 0);
+    const MixGroup &G = tab[g];
+    if (w >= G.code.n) continue;  // a ticket past this code's words
+    const int64_t li = gf - G.first;
+    const int64_t f = G.frames ? (int64_t)G.frames[li] : li;
+    int half = 0;
+    if (lane == 0) half = __ldcg(G.a.half_cur + f);
+    half = __shfl_sync(FULL, half, 0);
+    const int npl = G.npl;
+    int q;
+    if (npl == 1)
+      q = mixed_word<SYN, 1>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane, tally);
+    else if (npl == 2)
+      q = mixed_word<SYN, 2>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane, tally);
+    else
+      q = mixed_word<SYN, 4>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane, tally);
+    if (lane == 0 && q < 0) atomicExch(G.a.bad + f, 1);
+    __threadfence();  // release this word's L_E and hard decision
+    __syncwarp();
+    int done = 0;
+    if (lane == 0) done = atomicAdd(G.a.done_words + f, 1);
+    done = __shfl_sync(FULL, done, 0);
+    if (done != G.code.n - 1) continue;
+    // the check uses this warp's word area as laid out for the group's NPL
+    if (npl == 1)
+      frame_after_half<1>(G.code, G.a, m.ctrl, m.queue, f, gf, half,
+                          reinterpret_cast<uint64_t *>(wsm + Layout<1, SYN>::o_w), lane);
+    else if (npl == 2)
+      frame_after_half<2>(G.code, G.a, m.ctrl, m.queue, f, gf, half,
+                          reinterpret_cast<uint64_t *>(wsm + Layout<2, SYN>::o_w), lane);
+    else
+      frame_after_half<4>(G.code, G.a, m.ctrl, m.queue, f, gf, half,
+                          reinterpret_cast<uint64_t *>(wsm + Layout<4, SYN>::o_w), lane);
+  }
+  if (lane == 0) {
+    if (m.wsum && tally.wsum) atomicAdd(m.wsum, tally.wsum);
+    if (m.xf_count && tally.xf) atomicAdd(m.xf_count, tally.xf);
+  }
+}
+
+// List and counters of the mixed form: every listed frame queued for its
+// current half.  Frames of groups marked `fresh` start at half 1 with cleared
+// counters; others resume where they were parked.  With per-frame half_stop
+// arrays, a frame parks after `epoch_halves` halves of this launch.
+static __global__ void k_mixed_init(const MixArgs m, int epoch_halves) {
+  const int64_t slots = m.total * (int64_t)m.max_half;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
+    m.queue[i] = i < m.total ? (int32_t)(i + 1) : 0;
+    if (i < m.total) {
+      int g = 0;
+      while (g + 1 < m.ngroups && m.groups[g + 1].first <= i) g++;
+      const MixGroup &G = m.groups[g];
+      const int64_t li = i - G.first;
+      const int64_t f = G.frames ? (int64_t)G.frames[li] : li;
+      if (G.fresh) {
+        G.a.half_cur[f] = 1;
+        G.a.bad[f] = 0;
+        G.a.queries[f] = 0;
+        G.a.par_queries[f] = 0;
+      }
+      G.a.done_words[f] = 0;
+      G.a.hmax[f] = 0;
+      if (G.a.half_stop) G.a.half_stop[f] = G.a.half_cur[f] + epoch_halves - 1;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    m.ctrl[0] = (int32_t)m.total;  // next slot to reserve
+    m.ctrl[1] = 0;                 // word tickets drawn
+    m.ctrl[2] = 0;                 // frames finished or parked
+    m.ctrl[3] = 0;                 // error
+  }
 }
 
 // list and counters of the persistent form: every frame queued for half 1
@@ -513,43 +659,41 @@ inline cudaError_t set_smem(K kernel, int smem) {
 template <int NPL, class SYN>
 cudaError_t launch_decode(const DevCode &code, const SisoParams &P, const DecodeArgs &a, cudaStream_t s) {
   if (a.n_words <= 0) return cudaSuccess;
-  const int wb = warp_scratch_bytes<NPL, SYN>(code.jmax);
-  const int smem = wb * WARPS_PER_BLOCK;
-  auto kern = k_decode<NPL, SYN>;
+  const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
+  auto kern = code.minb == 8 ? k_decode<NPL, SYN, 8> : k_decode<NPL, SYN, 6>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = grid_for(kern, smem, a.n_words);
-  kern<<<grid, TPB, smem, s>>>(code, P, a, wb);
+  kern<<<grid, TPB, smem, s>>>(code, P, a);
   return cudaGetLastError();
 }
 
 template <int NPL, class SYN>
 cudaError_t launch_trace(const DevCode &code, const float *lam, int max_q, uint64_t *out, int32_t *count,
                          int32_t *c_out, cudaStream_t s) {
-  const int wb = warp_scratch_bytes<NPL, SYN>(code.jmax);
+  const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
   auto kern = k_trace<NPL, SYN>;
-  cudaError_t e = set_smem(kern, wb);
+  cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
-  kern<<<1, 32, wb, s>>>(code, lam, max_q, out, count, c_out, wb);
+  kern<<<1, 32, smem, s>>>(code, lam, max_q, out, count, c_out);
   return cudaGetLastError();
 }
 
 template <int NPL, class SYN>
 cudaError_t launch_product_half(const DevCode &code, const SisoParams &P, const ProductArgs &a, int half,
                                 cudaStream_t s) {
-  const int wb = warp_scratch_bytes<NPL, SYN>(code.jmax);
-  const int smem = wb * WARPS_PER_BLOCK;
+  const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
   const int64_t items = a.n_frames * code.n;
   if (half & 1) {
-    auto kern = k_product_half<NPL, SYN, true>;
+    auto kern = code.minb == 8 ? k_product_half<NPL, SYN, true, 8> : k_product_half<NPL, SYN, true, 6>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(code, P, a, half, wb);
+    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(code, P, a, half);
   } else {
-    auto kern = k_product_half<NPL, SYN, false>;
+    auto kern = code.minb == 8 ? k_product_half<NPL, SYN, false, 8> : k_product_half<NPL, SYN, false, 6>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(code, P, a, half, wb);
+    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(code, P, a, half);
   }
   return cudaGetLastError();
 }
@@ -577,9 +721,8 @@ cudaError_t launch_product_persistent(const DevCode &code, const SisoParams &P, 
   k_persistent_init<<<(int)std::min<int64_t>((a.n_frames + 255) / 256, 4096), 256, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int wb = warp_scratch_bytes<NPL, SYN>(code.jmax);
-  const int smem = wb * WARPS_PER_BLOCK;
-  auto kern = k_product_persistent<NPL, SYN>;
+  const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
+  auto kern = code.minb == 8 ? k_product_persistent<NPL, SYN, 8> : k_product_persistent<NPL, SYN, 6>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -588,7 +731,31 @@ cudaError_t launch_product_persistent(const DevCode &code, const SisoParams &P, 
   // every block resident at once, no more warps than words of the batch
   const int64_t want = (a.n_frames * code.n + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * occ, want));
-  kern<<<grid, TPB, smem, s>>>(code, P, a, wb);
+  kern<<<grid, TPB, smem, s>>>(code, P, a);
+  return cudaGetLastError();
+}
+
+// Mixed form.  `m.groups` is device memory; `host_groups` the same table on
+// the host.  epoch_halves <= 0: no parking.
+template <class SYN>
+cudaError_t launch_product_mixed(const MixArgs &m, const MixGroup *host_groups, int epoch_halves, cudaStream_t s) {
+  if (m.total <= 0) return cudaSuccess;
+  k_mixed_init<<<(int)std::min<int64_t>((m.total * m.max_half + 255) / 256, 4096), 256, 0, s>>>(
+      m, epoch_halves > 0 ? epoch_halves : m.max_half);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const int smem = WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16 + m.ngroups * (int)sizeof(MixGroup);
+  auto kern = k_product_mixed<SYN>;
+  e = set_smem(kern, smem);
+  if (e != cudaSuccess) return e;
+  int occ = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TPB, smem);
+  if (occ < 1) occ = 1;
+  int64_t words = 0;
+  for (int g = 0; g < m.ngroups; g++) words += host_groups[g].count * host_groups[g].code.n;
+  const int64_t want = (words + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * occ, want));
+  kern<<<grid, TPB, smem, s>>>(m);
   return cudaGetLastError();
 }
 

@@ -51,6 +51,36 @@ struct ProductArgs {
   int32_t *bad;               // [F] a non-finite input was seen
   int32_t *ctrl;              // [4] slots reserved, word tickets, finished frames, error
   int32_t max_spin;           // microseconds of accumulated back-off without work before giving up
+  int32_t *half_stop;         // [F] or null: park the frame after this half (serving epochs)
+};
+
+// Mixed form: groups of frames, one code per group, in one launch.
+struct MixGroup {
+  DevCode code;
+  SisoParams P;
+  ProductArgs a;           // the group's buffers, indexed by frame (buffer) index; queue/ctrl unused
+  const int32_t *frames;   // [count] buffer index of each listed frame, or null for 0..count-1
+  int64_t first;           // launch-wide index of the group's first listed frame
+  int64_t count;           // listed frames
+  int32_t npl;             // bits per lane of the code: 1, 2 or 4
+  int32_t fresh;           // 1: the listed frames start at half 1 with cleared counters
+};
+
+constexpr int MIX_MAX_GROUPS = 16;
+
+struct MixArgs {
+  const MixGroup *groups;  // [ngroups] device memory, ordered by `first` (each block copies it to shared memory)
+  int32_t ngroups;
+  int64_t total;           // listed frames over all groups
+  int32_t slot_n;          // word tickets per list slot: the largest n
+  int32_t max_half;        // the largest 2 * max iterations
+  int32_t wstride;         // shared bytes per warp: the largest per-warp layout of the groups
+  int32_t dpbytes;         // the block's remaining-mass area: the largest of the groups
+  int32_t *queue;          // [total * max_half]
+  int32_t *ctrl;           // [4]
+  int32_t max_spin;
+  int32_t *xf_count;
+  unsigned long long *wsum;
 };
 
 template <int NPL, class SYN>
@@ -73,6 +103,11 @@ cudaError_t launch_product_check(const DevCode &code, const ProductArgs &a, int 
 template <int NPL, class SYN>
 cudaError_t launch_product_persistent(const DevCode &code, const SisoParams &P, const ProductArgs &a, cudaStream_t s);
 
-int scratch_bytes(int npl, int syn_bytes, int jmax);
+template <class SYN>
+cudaError_t launch_product_mixed(const MixArgs &m, const MixGroup *host_groups, int epoch_halves, cudaStream_t s);
+
+// shared-memory layout sizes of a code: per warp, and the block's remaining-mass area
+int warp_area_bytes(int npl, int syn_bytes);
+int dp_area_bytes(int npl, int syn_bytes, int jmax);
 
 }  // namespace sg

@@ -37,6 +37,7 @@ struct DevCode {
   const uint64_t *hrow;  // [m][nm] rows of H as bit masks over the n positions
   DevOrder ord;
   int32_t jmax;          // largest stored cost + 2 (bounds the remaining-mass DP)
+  int32_t minb;          // schedule: resident blocks per SM the kernels are compiled for (6 or 8)
 };
 
 struct SisoParams {

@@ -191,6 +191,9 @@ struct RankRec {
   float t;
 };
 
+// Shared memory of a block: one area per warp (below), then one
+// remaining-mass area for the whole block (the cost DP, needed by about 0.2%
+// of component decodings) guarded by a lock word.
 template <int NPL, class SYN>
 struct Layout {
   static constexpr int NT = 32 * NPL;
@@ -202,31 +205,67 @@ struct Layout {
   static constexpr int o_lp = o_cw + 8 * LMAX * NM;                   // float[LMAX] log p(z)/p(0)
   static constexpr int o_wl = o_lp + 4 * LMAX;                        // float[LMAX] APP of each listed word
   static constexpr int o_perm = o_wl + 4 * LMAX;                      // u8[NT] rank -> bit
-  static constexpr int o_tail = align16(o_perm + NT);
-  // tail area (sized for the 8-byte XF policy): sfac[NT+1], fu[NT+1], fb[NT+1], ek[J] (float), he[J], ho[J]
-  static __host__ __device__ int bytes(int jm) { return align16(o_tail + 24 * (NT + 1) + 20 * jm + 32); }
+  static constexpr int o_w = align16(o_perm + NT);                    // u64[NT][NM] words of a frame (check)
+  static constexpr int warp_bytes = align16(o_w + 8 * NT * NM);
+  // block area (sized for the 8-byte XF policy): sfac[NT+1], fu[NT+1], fb[NT+1], ek[J] (float), he[J], ho[J]
+  static __host__ __device__ int dp_bytes(int jm) { return align16(24 * (NT + 1) + 20 * jm + 32); }
+  // a block of WARPS_PER_BLOCK warps: their areas, the remaining-mass area and its lock word
+  static __host__ __device__ int block_bytes(int jm) { return WARPS_PER_BLOCK * warp_bytes + dp_bytes(jm) + 16; }
 };
 
+// A warp's view of the block's shared memory: its own area and the block's
+// remaining-mass area with its lock word.  Only the two base addresses are
+// kept; every array is a fixed offset from them.
 template <int NPL, class SYN>
 struct Scratch {
   using LY = Layout<NPL, SYN>;
-  float *l2, *al;
-  RankRec<SYN> *hr;
-  uint64_t *cw;
-  float *lp, *wl;
-  uint8_t *perm;
-  unsigned char *tail;
-  __device__ void bind(unsigned char *base) {
-    l2 = reinterpret_cast<float *>(base + LY::o_l2);
-    al = reinterpret_cast<float *>(base + LY::o_al);
-    hr = reinterpret_cast<RankRec<SYN> *>(base + LY::o_hr);
-    cw = reinterpret_cast<uint64_t *>(base + LY::o_cw);
-    lp = reinterpret_cast<float *>(base + LY::o_lp);
-    wl = reinterpret_cast<float *>(base + LY::o_wl);
-    perm = base + LY::o_perm;
-    tail = base + LY::o_tail;
+  unsigned char *base;  // this warp's area
+  unsigned char *dp;    // the block's remaining-mass area, followed by its lock word
+  int dpbytes;
+  __device__ void bind(unsigned char *warp_area, unsigned char *dp_area, int dp_bytes) {
+    base = warp_area;
+    dp = dp_area;
+    dpbytes = dp_bytes;
   }
+  __device__ float *l2() const { return reinterpret_cast<float *>(base + LY::o_l2); }
+  __device__ float *al() const { return reinterpret_cast<float *>(base + LY::o_al); }
+  __device__ RankRec<SYN> *hr() const { return reinterpret_cast<RankRec<SYN> *>(base + LY::o_hr); }
+  __device__ uint64_t *cw() const { return reinterpret_cast<uint64_t *>(base + LY::o_cw); }
+  __device__ float *lp() const { return reinterpret_cast<float *>(base + LY::o_lp); }
+  __device__ float *wl() const { return reinterpret_cast<float *>(base + LY::o_wl); }
+  __device__ uint8_t *perm() const { return base + LY::o_perm; }
+  __device__ uint64_t *W() const { return reinterpret_cast<uint64_t *>(base + LY::o_w); }
+  __device__ unsigned char *tail() const { return dp; }
+  __device__ int *lock() const { return reinterpret_cast<int *>(dp + dpbytes); }
 };
+
+// The block's remaining-mass area is taken by one warp at a time.  Its holder
+// runs a bounded computation that waits for nothing, so the wait ends; the
+// bound (about 4 s) only keeps a broken state from spinning for ever: the
+// warp then proceeds without the lock and reports it (returns false).
+__device__ __forceinline__ bool dp_lock(int *lock, int lane) {
+  int ok = 1;
+  if (lane == 0) {
+    unsigned nap = 32;
+    long long tries = 0;
+    while (atomicCAS(lock, 0, 1) != 0) {
+      if (++tries > (1ll << 22)) {
+        ok = 0;
+        break;
+      }
+      __nanosleep(nap);
+      if (nap < 1024) nap <<= 1;
+    }
+  }
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  __threadfence_block();
+  return ok != 0;
+}
+__device__ __forceinline__ void dp_unlock(int *lock, bool held, int lane) {
+  __syncwarp();
+  __threadfence_block();
+  if (lane == 0 && held) atomicExch(lock, 0);
+}
 
 // ----------------------------------------------------------------------------
 // warp helpers
@@ -516,7 +555,7 @@ __device__ __noinline__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN>
                                             int n, int c, int cls, int Cs, float g2, int lane) {
   using T = typename Ops::T;
   constexpr int NT = 32 * NPL;
-  T *sfac = reinterpret_cast<T *>(sc.tail);
+  T *sfac = reinterpret_cast<T *>(sc.tail());
   T *fu = sfac + NT + 1;
   T *fb = fu + NT + 1;
   float *ek = reinterpret_cast<float *>(fb + NT + 1);
@@ -534,7 +573,7 @@ __device__ __noinline__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN>
     if (q < tc) in = __ldg(O.cost + tb + q) == (uint16_t)Cs;
     if (in) {
       const uint4 e = __ldg(O.ent + tb + q);
-      const float s2 = ent_sum(e, e.x & 0xff, sc.l2);
+      const float s2 = ent_sum(e, e.x & 0xff, sc.l2());
       acc = Ops::add(acc, Ops::from_log2(g2Cs - s2));
     }
     if (!__all_sync(FULL, in)) break;  // costs are nondecreasing
@@ -551,10 +590,10 @@ __device__ __noinline__ typename Ops::T remaining_scaled(const Scratch<NPL, SYN>
       const int e = lane * NPL + k;
       T t = Ops::zero();
       if (e < n) {
-        t = Ops::from_log2(-sc.l2[e]);
+        t = Ops::from_log2(-sc.l2()[e]);
         // factor used by the tail: low ranks t * 2^(g2 d_e), high ranks t * 2^(g2 Cs)
         const float d = (float)(e + 1 + c);
-        sfac[e] = Ops::from_log2((e < R0 ? g2 * d : g2Cs) - sc.l2[e]);
+        sfac[e] = Ops::from_log2((e < R0 ? g2 * d : g2Cs) - sc.l2()[e]);
       }
       const T nu = Ops::fma(b, t, u);
       const T nb = Ops::fma(u, t, Ops::add(b, t));
@@ -653,7 +692,7 @@ __device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, in
   for (int k = 0; k < NPL; k++) {
     const int e = lane * NPL + k;
     if (e < n) {
-      const float t = sc.hr[e].t;
+      const float t = sc.hr()[e].t;
       const DF nu = df_add_pos(u, df_mul_f(b, t));
       const DF nb = df_add_pos(df_add_pos(b, DF{t, 0.f}), df_mul_f(u, t));
       u = nu;
@@ -674,6 +713,8 @@ __device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, in
 }
 
 // log2 of the remaining (unqueried) mass relative to p(0^n|r); warp-uniform.
+// *used_xf (if given) gets bit 0 when the extended-range sum was needed and
+// bit 1 when the block's remaining-mass area could not be locked.
 // tq is the queried mass of the nonzero patterns (double-float, summed over
 // the warp, the same value in every lane).  The class total minus tq is used
 // when it is well conditioned: in FP32 when the difference is at least 2% of
@@ -691,7 +732,7 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
     for (int k = 0; k < NPL; k++) {
       const int e = lane * NPL + k;
       if (e < n) {
-        const float t = sc.hr[e].t;
+        const float t = sc.hr()[e].t;
         const float nu = fmaf(b, t, u), nb = fmaf(u, t, b + t);
         u = nu;
         b = nb;
@@ -732,16 +773,24 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
   const int Cs = __ldg(O.cost + tb + qs);
   const int R0 = min(max(Cs - c, 0), n);
   float g = CUDART_INF_F;
-  for (int e = lane; e < R0; e += 32) g = fminf(g, sc.l2[e] / (float)(e + 1 + c));
+  for (int e = lane; e < R0; e += 32) g = fminf(g, sc.l2()[e] / (float)(e + 1 + c));
   g = __shfl_sync(FULL, warp_min_f(g), 0);
   if (!(g < CUDART_INF_F)) g = 0.f;
+  const bool held = dp_lock(sc.lock(), lane);
+  float out;
   const float tot = __shfl_sync(FULL, remaining_scaled<FOps, NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, g, lane), 0);
-  if (tot >= 0x1p-60f && tot < CUDART_INF_F) return log2f(tot) - g * (float)Cs;
-  if (used_xf) *used_xf = 1;
+  if (tot >= 0x1p-60f && tot < CUDART_INF_F) {
+    out = log2f(tot) - g * (float)Cs;
+  } else {
+    if (used_xf) *used_xf |= 1;
 #ifdef SG_PHASE_PROFILE
-  if (lane == 0) SG_PROF(8, 1);
+    if (lane == 0) SG_PROF(8, 1);
 #endif
-  return remaining_log2_xf<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, lane);
+    out = remaining_log2_xf<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, lane);
+  }
+  dp_unlock(sc.lock(), held, lane);
+  if (!held && used_xf) *used_xf |= 2;
+  return out;
 }
 
 // numerically safe log(exp(a) + exp(b)) (natural log, -inf aware)
@@ -811,10 +860,10 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
       const float a = __uint_as_float((unsigned)(key[k] >> 32));
       const int idx = (int)(key[k] & 0xffffffffu);
       const float l2v = __fmul_rn(a, LOG2E_F);
-      sc.al[e] = a;
-      sc.l2[e] = l2v;
-      sc.perm[e] = (uint8_t)idx;
-      sc.hr[e] = RankRec<SYN>{(SYN)__ldg(code.hcol + idx), exp2f(-l2v)};
+      sc.al()[e] = a;
+      sc.l2()[e] = l2v;
+      sc.perm()[e] = (uint8_t)idx;
+      sc.hr()[e] = RankRec<SYN>{(SYN)__ldg(code.hcol + idx), exp2f(-l2v)};
       const int64_t qa = quant256(a);
       sy += qa;
       sxy += qa * (e + 1);
@@ -825,7 +874,7 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
   sxy = ((int64_t)__reduce_add_sync(FULL, (unsigned)(sxy >> 24)) << 24) +
         (int64_t)__reduce_add_sync(FULL, (unsigned)(sxy & 0xffffff));
   h.c = one_line_c(sy, sxy, n, code.c_max);
-  if (lane == 0) sc.hr[n] = RankRec<SYN>{(SYN)0, 1.f};  // neutral record for unused entry bytes
+  if (lane == 0) sc.hr()[n] = RankRec<SYN>{(SYN)0, 1.f};  // neutral record for unused entry bytes
   __syncwarp();
   return true;
 }
@@ -877,7 +926,7 @@ __device__ __forceinline__ float warp_sum_f(float x) {
 }
 
 // Record the hit of lane hl as list entry `slot`: the codeword y + z in bit
-// order (sc.cw) and log p(z)/p(0) = -sum |lambda| over z (sc.lp).  The
+// order (sc.cw()) and log p(z)/p(0) = -sum |lambda| over z (sc.lp()).  The
 // pattern is broadcast and lane k handles its k-th rank.
 template <int NPL, class SYN>
 __device__ __forceinline__ void record_hit(const Scratch<NPL, SYN> &sc, const WordHead<NPL, SYN> &h, const uint4 &e,
@@ -893,16 +942,16 @@ __device__ __forceinline__ void record_hit(const Scratch<NPL, SYN> &sc, const Wo
   const unsigned wd = byte < 4 ? b.x : (byte < 8 ? b.y : (byte < 12 ? b.z : b.w));
   const bool mine = lane < w;
   const int r = mine ? (wd >> (8 * (byte & 3))) & 0xff : 0;
-  const float ls = warp_sum_f(mine ? sc.al[r] : 0.f);
-  const int bi = mine ? sc.perm[r] : 0;
+  const float ls = warp_sum_f(mine ? sc.al()[r] : 0.f);
+  const int bi = mine ? sc.perm()[r] : 0;
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
     const unsigned word = __reduce_or_sync(FULL, (mine && (bi >> 5) == k) ? 1u << (bi & 31) : 0u) ^ h.yb[k];
-    if (lane == 0) reinterpret_cast<unsigned *>(sc.cw + slot * NM)[k] = word;
+    if (lane == 0) reinterpret_cast<unsigned *>(sc.cw() + slot * NM)[k] = word;
   }
   if (lane == 0) {
-    if (NPL & 1) reinterpret_cast<unsigned *>(sc.cw + slot * NM)[NPL] = 0u;  // upper half of the last u64
-    sc.lp[slot] = -ls;
+    if (NPL & 1) reinterpret_cast<unsigned *>(sc.cw() + slot * NM)[NPL] = 0u;  // upper half of the last u64
+    sc.lp()[slot] = -ls;
   }
   __syncwarp();
 }
@@ -915,7 +964,7 @@ __device__ __forceinline__ bool thr_reached(const float *lp, int nhit, float M, 
 }
 template <int NPL, class SYN>
 __device__ __forceinline__ bool thr_reached(const Scratch<NPL, SYN> &sc, int nhit, float M, float thr) {
-  return thr_reached(sc.lp, nhit, M, thr);
+  return thr_reached(sc.lp(), nhit, M, thr);
 }
 
 // eq. LLRi in the log domain for a bit whose linear sums underflowed (out of line: rare)
@@ -925,10 +974,10 @@ __device__ __noinline__ float lapp_logdomain(const Scratch<NPL, SYN> &sc, int nh
   float b0 = M - softplus(-x), b1 = M - softplus(x);
   const uint64_t bitm = 1ull << (i & 63);
   for (int l = 0; l < nhit; l++) {
-    if (sc.cw[l * NM + (i >> 6)] & bitm)
-      b1 = lse(b1, sc.lp[l]);
+    if (sc.cw()[l * NM + (i >> 6)] & bitm)
+      b1 = lse(b1, sc.lp()[l]);
     else
-      b0 = lse(b0, sc.lp[l]);
+      b0 = lse(b0, sc.lp()[l]);
   }
   return b0 - b1;
 }
@@ -936,12 +985,14 @@ __device__ __noinline__ float lapp_logdomain(const Scratch<NPL, SYN> &sc, int nh
 // lam[k] is bit lane + 32k of the SISO input lambda = fl32(L_Ch + L_A)
 // (the caller loads it; entries past n are ignored).  On return lapp[k] holds
 // L_APP for the same bits, res the per-word results; the list (in query
-// order) is left in the scratch: sc.cw (codewords, natural bit order),
-// sc.lp (log p(z)/p(0)) and sc.wl (APP of each word).
+// order) is left in the scratch: sc.cw() (codewords, natural bit order),
+// sc.lp() (log p(z)/p(0)) and sc.wl() (APP of each word).  *flags (if given)
+// collects the remaining-mass flags (bit 0: extended range; bit 1: the
+// block's remaining-mass area could not be locked).
 template <int NPL, class SYN>
 __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratch<NPL, SYN> &sc,
                           const float (&lam)[NPL], int lane, float (&lapp)[NPL], WordResult &res,
-                          int *xf_count = nullptr) {
+                          int *flags = nullptr) {
   constexpr int NT = 32 * NPL;
   constexpr int NM = (NT + 63) / 64;
   const int n = code.n;
@@ -986,7 +1037,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     const int w = e.x & 0xff;
     const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
     DF mass;
-    const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr, mass) ^ h.s0;
+    const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr(), mass) ^ h.s0;
     const bool hit = lane < lim && s == 0;
     unsigned hm = __ballot_sync(FULL, hit);
     int stop_lane = -1;
@@ -1003,7 +1054,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
         DF part = tmass;
         if (lane <= hl) df_acc(part, mass);
         const DF tq = df_warp_sum(part);
-        const float r2 = remaining_log2<NPL, SYN>(sc, O, tb, tc, q + hl, n, h.c, cls, lane, tq, xf_count);
+        const float r2 = remaining_log2<NPL, SYN>(sc, O, tb, tc, q + hl, n, h.c, cls, lane, tq, flags);
         if (thr_reached(sc, nhit, r2 * LN2_F + code.log_phi, P.thr)) {
           stop_lane = hl;
           lr2 = r2;
@@ -1035,7 +1086,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   if (!have_lr2)
     lr2 = exhausted ? -CUDART_INF_F
                     : remaining_log2<NPL, SYN>(sc, O, tb, tc, q - 1, n, h.c, cls, lane, df_warp_sum(tmass),
-                                               xf_count);
+                                               flags);
 #ifdef SG_PHASE_PROFILE
   const long long t3 = clock64();
 #endif
@@ -1051,15 +1102,15 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   } else {
     // log(R phi + sum_l p_l), all relative to p(0): max plus log of a sum
     float mx = M;
-    for (int l = 0; l < nhit; l++) mx = fmaxf(mx, sc.lp[l]);
+    for (int l = 0; l < nhit; l++) mx = fmaxf(mx, sc.lp()[l]);
     float sum = M == -CUDART_INF_F ? 0.f : expf(M - mx);
-    for (int l = 0; l < nhit; l++) sum += expf(sc.lp[l] - mx);
+    for (int l = 0; l < nhit; l++) sum += expf(sc.lp()[l] - mx);
     const float D = mx + logf(sum);
     res.logD = D;
     const float pm = M == -CUDART_INF_F ? 0.f : expf(M - D);
     res.pmiss = pm;
     // APP of each listed word (list weights relative to the normaliser)
-    if (lane < nhit) sc.wl[lane] = expf(sc.lp[lane] - D);
+    if (lane < nhit) sc.wl()[lane] = expf(sc.lp()[lane] - D);
     __syncwarp();
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
@@ -1072,10 +1123,10 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
       float a1 = pm * (x >= 0.f ? sn : sp);              // miss term, bit 1
       const uint64_t bitm = 1ull << (i & 63);
       for (int l = 0; l < nhit; l++) {
-        if (sc.cw[l * NM + (i >> 6)] & bitm)
-          a1 += sc.wl[l];
+        if (sc.cw()[l * NM + (i >> 6)] & bitm)
+          a1 += sc.wl()[l];
         else
-          a0 += sc.wl[l];
+          a0 += sc.wl()[l];
       }
       // both sums lie in (1e-30, 1 + 1e-6]: __fdividef's range, 2 ulp
       lapp[k] = (a0 > 1e-30f && a1 > 1e-30f) ? logf(__fdividef(a0, a1)) : lapp_logdomain<NPL, SYN>(sc, nhit, M, x, i);

@@ -48,4 +48,7 @@ def test_argument_errors_without_gpu(lib):
     assert lib.sogrand_code_create(8, 7, None, 1, C.byref(h)) == _lib.EINVAL
     assert lib.sogrand_decode(None, 1, None, None, 4, 10, 0.0, *([None] * 8), None) == _lib.EINVAL
     assert lib.product_decode(None, None, 1, None, 4, 10, 0.0, 0.5, 4, None, None, None, None, None) == _lib.EINVAL
+    assert lib.product_decode_mixed(0, None, 4, 10, 0.0, 0.5, 4, None, None) == _lib.EINVAL
+    assert lib.product_decode_mixed(17, (_lib.FrameGroup * 17)(), 4, 10, 0.0, 0.5, 4, None, None) == _lib.EINVAL
+    assert lib.sogrand_int_peak(0, None, None, None) == _lib.EINVAL
     assert lib.sogrand_strerror(_lib.EUNSUPPORTED).decode() == "unsupported configuration"

@@ -192,3 +192,67 @@ def test_host_entry_equals_device_entry(env, F, pinned):
     assert out["status"][F // 3] == 2
     sg.sogrand_release_cached()
     c.close()
+
+
+def test_mixed_form_equals_each_code_alone(env):
+    """Frames of eBCH(32,26)^2, (64,51)^2 and (128,120)^2 in 4:2:1 proportion,
+    Eb/N0 uniform in 2.5..4 dB per frame, decoded by one mixed launch, give
+    exactly what product_decode_persistent gives for each code alone."""
+    torch, sg = env
+    rng = np.random.default_rng(77)
+    specs = [("ebch_32_26", 48), ("ebch_64_51", 24), ("ebch_128_120", 12)]
+    groups, refs, codes = [], [], []
+    for i, (name, F) in enumerate(specs):
+        code = ebch(name)
+        U, X, lch = awgn_frames(code, F, rng.uniform(2.5, 4.0, F), seed=800 + i)
+        if i == 1:
+            lch[5, 0, 0] = np.nan
+        c = sg.Code.from_linear_code(code)
+        d = torch.from_numpy(lch).cuda()
+        r = sg.product_decode(c, d, L=4, query_cap=10**4, alpha=0.5, max_iter=20, persistent=True)
+        torch.cuda.synchronize()
+        refs.append({k: v.cpu().numpy() for k, v in r.items() if hasattr(v, "cpu")})
+        groups.append((c, d))
+        codes.append(c)
+    outs, info = sg.product_decode_mixed(groups, L=4, query_cap=10**4, alpha=0.5, max_iter=20)
+    torch.cuda.synchronize()
+    for (name, F), o, r in zip(specs, outs, refs):
+        for key in ("bits", "half_iters", "status", "queries"):
+            np.testing.assert_array_equal(o[key].cpu().numpy(), r[key], err_msg=f"{name} {key}")
+    assert outs[1]["status"][5].item() == 2
+    assert info["launches"] == 2 and info["timing_ms"] > 0
+    # groups needing 32-bit and 64-bit syndromes cannot share a launch
+    H = np.random.default_rng(5).integers(0, 2, (40, 64)).astype(np.uint8)
+    wide = sg.Code(H, even=False)
+    with pytest.raises(sg.SograndError):
+        sg.product_decode_mixed([groups[0], (wide, torch.zeros((1, 64, 64), device="cuda"))])
+    wide.close()
+    for c in codes:
+        c.close()
+
+
+@pytest.mark.parametrize("name", ["ebch_64_57", "ebch_64_51", "ebch_32_26"])
+def test_schedules_give_identical_results_and_tuner_picks_one(env, name):
+    """The two compiled schedules (6 or 8 resident blocks per SM) run the same
+    arithmetic; the autotuner keeps the faster one for the code."""
+    torch, sg = env
+    code = ebch(name)
+    U, X, lch = awgn_frames(code, 400, 2.75, seed=900)
+    c = sg.Code.from_linear_code(code)
+    d = torch.from_numpy(lch).cuda()
+    outs = []
+    for minb in (6, 8):
+        assert c.schedule(minb) == minb
+        for persistent in (True, False):
+            o = sg.product_decode(c, d, L=4, query_cap=10**4, alpha=0.5, max_iter=10, persistent=persistent)
+            torch.cuda.synchronize()
+            outs.append({k: v.cpu().numpy() for k, v in o.items() if hasattr(v, "cpu")})
+    for o in outs[1:]:
+        for key in ("bits", "half_iters", "status", "queries", "weight_sum"):
+            np.testing.assert_array_equal(o[key], outs[0][key], err_msg=key)
+    chosen, ms = c.tune(d, max_iter=10)
+    assert chosen in (6, 8) and c.schedule() == chosen and min(ms) > 0
+    assert ms[(6, 8).index(chosen)] == min(ms)
+    with pytest.raises(sg.SograndError):
+        c.schedule(7)
+    c.close()
