@@ -319,6 +319,67 @@ int sogrand_trace_patterns(sogrand_code *code, const float *llr, int64_t max_q, 
                            int64_t *n_out, int32_t *c_out);
 
 /*
+ * Serving loop: continuous batching of product-decode requests (the turbo
+ * decoder of Sec. VI as a service; the paper has no serving system).
+ *
+ * A server owns, per registered code, a device pool of `slots[i]` frame slots
+ * (channel LLRs, L_E state, hard decisions and counters of a frame stay
+ * resident there across half iterations: about 8 n^2 + 8 n ceil(n/64) +
+ * n^2/8 + 16 max_iter + 60 bytes a slot, allocated at creation: the memory
+ * budget).  A worker thread drives each pool: when its previous launch has
+ * finished it retires the frames that stopped, completes requests whose last
+ * frame stopped (copying their outputs to the caller's host buffers), admits
+ * waiting requests of that code in arrival order while free slots last
+ * (copying their LLRs in), and launches the batched decoder over every
+ * resident frame for at most `epoch_halves` half iterations; frames that need
+ * more stay parked in their slots.  Pools launch on their own streams, so
+ * requests of different codes decode concurrently, and a request that arrives
+ * while others are decoding joins at its pool's next epoch.  Every frame runs
+ * the arithmetic of product_decode_persistent, so its results are the same
+ * alone and in any mix.  Decode parameters are the server's.
+ *
+ *   codes[n_codes]   registered codes (1..16; each is the row and column code
+ *                    of its requests); slots[n_codes] frames each pool holds
+ *   epoch_halves     1 .. 2 max_iter
+ * Errors: EINVAL, ENOMEM (a pool does not fit), ECUDA.
+ */
+typedef struct sogrand_server sogrand_server;
+int sogrand_server_create(int n_codes, sogrand_code *const *codes, const int64_t *slots, int L, int64_t query_cap,
+                          float thr, float alpha, int max_iter, int epoch_halves, sogrand_server **out);
+
+/*
+ * Queue a request of n_frames frames of registered code `code_index`.
+ *   llr        HOST [n_frames][n][n] channel LLRs (pinned memory recommended);
+ *              read when the request is admitted: keep it until completion
+ *   bits       HOST [n_frames][ceil(n*n/8)] out (required)
+ *   half_iters, status, queries  HOST [n_frames] out, or NULL
+ *   ticket     HOST out: identifies the request for sogrand_server_wait
+ * Outputs are written before the request is reported done.  Errors: EINVAL
+ * (bad arguments, n_frames above the pool's slots, server stopping), the
+ * server's error if it has failed.
+ */
+int sogrand_server_submit(sogrand_server *server, int code_index, int64_t n_frames, const float *llr, uint8_t *bits,
+                          int32_t *half_iters, uint8_t *status, int64_t *queries, int64_t *ticket);
+
+/*
+ * Wait up to timeout_ms (<= 0: do not wait) for a request.  *done = 1 when it
+ * has completed; then *latency_ms (may be NULL) is the time from submission to
+ * completion (outputs in host memory) and the request's record is released
+ * (a ticket is reported done once).  Returns the request's status once done
+ * (SOGRAND_OK, ETIMEOUT if its launch hit the bounded-wait limit, ECUDA),
+ * else SOGRAND_OK.  Errors: EINVAL (unknown or already reported ticket).
+ */
+int sogrand_server_wait(sogrand_server *server, int64_t ticket, int timeout_ms, int *done, double *latency_ms);
+
+/* Counters (each may be NULL).  Returns the server's error state. */
+int sogrand_server_stats(sogrand_server *server, int64_t *launches, int64_t *frames_done, int64_t *requests_done,
+                         int64_t *frames_resident, int64_t *requests_waiting);
+
+/* Finish every submitted request, stop the worker and free the pools.
+ * Returns the server's error state. */
+int sogrand_server_destroy(sogrand_server *server);
+
+/*
  * Device scratch of the decoders (the per-frame L_E state and counters) comes
  * from one stream-ordered memory pool per device that the library creates on
  * first use and that keeps freed memory for the next call.  This returns the

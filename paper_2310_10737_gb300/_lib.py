@@ -65,6 +65,12 @@ def load() -> C.CDLL:
                                                 C.POINTER(ProductStats), vp]
         L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.sogrand_release_cached.argtypes = []
+        L.sogrand_server_create.argtypes = [i32, C.POINTER(vp), C.POINTER(C.c_int64), i32, i64, f32, f32, i32, i32,
+                                            C.POINTER(vp)]
+        L.sogrand_server_submit.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, C.POINTER(C.c_int64)]
+        L.sogrand_server_wait.argtypes = [vp, i64, i32, C.POINTER(C.c_int), C.POINTER(C.c_double)]
+        L.sogrand_server_stats.argtypes = [vp] + [C.POINTER(C.c_int64)] * 5
+        L.sogrand_server_destroy.argtypes = [vp]
         L.sogrand_code_schedule.argtypes = [vp, i32, C.POINTER(C.c_int)]
         L.sogrand_code_tune.argtypes = [vp, i64, vp, i32, i64, f32, f32, i32, C.POINTER(C.c_int),
                                         C.POINTER(C.c_float), vp]
@@ -76,7 +82,8 @@ def load() -> C.CDLL:
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
                      "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak",
-                     "product_decode_mixed", "sogrand_code_schedule", "sogrand_code_tune"):
+                     "product_decode_mixed", "sogrand_code_schedule", "sogrand_code_tune", "sogrand_server_create",
+                     "sogrand_server_submit", "sogrand_server_wait", "sogrand_server_stats", "sogrand_server_destroy"):
             getattr(L, name).restype = C.c_int
         _lib = L
         return L
@@ -280,6 +287,70 @@ def product_decode_host(code: Code, llr_ch: np.ndarray, L: int = 4, query_cap: i
                                     hp(out["status"]), hp(out["queries"]), _stream(stream))
     _check(rc, "product_decode_host")
     return out
+
+
+class Server:
+    """Continuous-batching decode server (sogrand_server_*): requests of
+    registered codes are admitted into device-resident frame slots as they
+    free up and decoded in epochs of half iterations."""
+
+    def __init__(self, codes, slots, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
+                 max_iter: int = 20, epoch_halves: int = 2):
+        self.codes = list(codes)
+        hs = (C.c_void_p * len(self.codes))(*[c.handle for c in self.codes])
+        sl = (C.c_int64 * len(self.codes))(*[int(x) for x in slots])
+        h = C.c_void_p()
+        _check(load().sogrand_server_create(len(self.codes), hs, sl, int(L), int(query_cap), float(thr), float(alpha),
+                                            int(max_iter), int(epoch_halves), C.byref(h)), "sogrand_server_create")
+        self._h = h
+        self._keep = {}
+
+    def submit(self, code_index: int, llr, out=None):
+        """Queue host frames [F, n, n] float32 (numpy or pinned torch); returns (ticket, out dict of host arrays)."""
+        code = self.codes[code_index]
+        F, n, _ = llr.shape
+        assert n == code.n
+        if out is None:
+            out = dict(bits=np.empty((F, (n * n + 7) // 8), np.uint8), half_iters=np.empty(F, np.int32),
+                       status=np.empty(F, np.uint8), queries=np.empty(F, np.int64))
+
+        def hp(a):
+            return C.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data_as(C.c_void_p)
+
+        t = C.c_int64(0)
+        _check(load().sogrand_server_submit(self._h, int(code_index), int(F), hp(llr), hp(out["bits"]),
+                                            hp(out["half_iters"]), hp(out["status"]), hp(out["queries"]),
+                                            C.byref(t)), "sogrand_server_submit")
+        self._keep[t.value] = (llr, out)
+        return t.value, out
+
+    def wait(self, ticket: int, timeout_ms: int = 60000):
+        """(done, latency_ms); raises SograndError if the request failed."""
+        done, lat = C.c_int(0), C.c_double(0)
+        rc = load().sogrand_server_wait(self._h, int(ticket), int(timeout_ms), C.byref(done), C.byref(lat))
+        if done.value:
+            self._keep.pop(ticket, None)
+        _check(rc, "sogrand_server_wait")
+        return bool(done.value), lat.value
+
+    def stats(self):
+        v = [C.c_int64(0) for _ in range(5)]
+        load().sogrand_server_stats(self._h, *[C.byref(x) for x in v])
+        return dict(zip(("launches", "frames_done", "requests_done", "frames_resident", "requests_waiting"),
+                        [x.value for x in v]))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            rc = load().sogrand_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+            _check(rc, "sogrand_server_destroy")
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def sogrand_release_cached():

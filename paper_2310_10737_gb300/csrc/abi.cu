@@ -348,6 +348,28 @@ int ensure_cap(sogrand_code *c, int64_t cap) {
 
 }  // namespace
 
+// Accessors for the serving loop (server.cu), which sees codes only through these.
+namespace sgi {
+sg::DevCode dev_code_of(const sogrand_code *c) { return dev_code(c); }
+int code_n(const sogrand_code *c) { return c->n; }
+int code_nm(const sogrand_code *c) { return c->nm; }
+int code_m(const sogrand_code *c) { return c->m; }
+int ensure_code_cap(sogrand_code *c, int64_t cap) { return ensure_cap(c, cap); }
+cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P, const sg::ProductArgs &a,
+                                  cudaStream_t s) {
+  const sg::DevCode d = dev_code(c);
+  cudaError_t e = cudaSuccess;
+  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, P, a, s)));
+  return e;
+}
+int sm_count_of_device() {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms > 0 ? sms : 1;
+}
+}  // namespace sgi
+
 namespace sg {
 int warp_area_bytes(int npl, int syn_bytes) {
   if (npl == 1) return syn_bytes == 4 ? Layout<1, uint32_t>::warp_bytes : Layout<1, uint64_t>::warp_bytes;

@@ -469,7 +469,8 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
   for (;;) {
     int slot, w, f1;
     if (!sched_take(a.ctrl, a.queue, nslots, a.n_frames, n, a.max_spin, lane, &slot, &w, &f1)) break;
-    const int64_t f = (int64_t)f1 - 1;
+    const int64_t li = (int64_t)f1 - 1;  // list index
+    const int64_t f = a.frame_list ? (int64_t)a.frame_list[li] : li;
     int half = 0;
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
     if (lane == 0) done = atomicAdd(a.done_words + f, 1);
     done = __shfl_sync(FULL, done, 0);
     if (done != n - 1) continue;
-    frame_after_half<NPL>(code, a, a.ctrl, a.queue, f, f, half, sc.W(), lane);
+    frame_after_half<NPL>(code, a, a.ctrl, a.queue, f, li, half, sc.W(), lane);
   }
   tally.flush(a, lane);
 }
@@ -608,12 +609,24 @@ static __global__ void k_persistent_init(const ProductArgs a) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
     queue[i] = i < F ? (int32_t)(i + 1) : 0;
     if (i < F) {
-      a.half_cur[i] = 1;
-      a.done_words[i] = 0;
-      a.bad[i] = 0;
-      a.hmax[i] = 0;
-      a.queries[i] = 0;
-      a.par_queries[i] = 0;
+      int64_t f = i;
+      bool fresh = true;
+      if (a.frame_list) {
+        const int32_t e = a.frame_list[i];
+        fresh = e < 0;
+        f = fresh ? -(int64_t)e - 1 : (int64_t)e;
+        if (fresh) a.frame_list[i] = (int32_t)f;
+      }
+      if (fresh) {
+        a.half_cur[f] = 1;
+        a.bad[f] = 0;
+        a.queries[f] = 0;
+        a.par_queries[f] = 0;
+        if (a.frame_list) a.status[f] = 255;  // in progress until the frame finishes
+      }
+      a.done_words[f] = 0;
+      a.hmax[f] = 0;
+      if (a.half_stop) a.half_stop[f] = a.half_cur[f] + a.epoch_halves - 1;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -730,7 +743,9 @@ cudaError_t launch_product_persistent(const DevCode &code, const SisoParams &P, 
   if (occ < 1) occ = 1;
   // every block resident at once, no more warps than words of the batch
   const int64_t want = (a.n_frames * code.n + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * occ, want));
+  int64_t cap = (int64_t)sm_count() * occ;
+  if (a.grid_cap > 0 && a.grid_cap < cap) cap = a.grid_cap;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
   kern<<<grid, TPB, smem, s>>>(code, P, a);
   return cudaGetLastError();
 }

@@ -52,6 +52,13 @@ struct ProductArgs {
   int32_t *ctrl;              // [4] slots reserved, word tickets, finished frames, error
   int32_t max_spin;           // microseconds of accumulated back-off without work before giving up
   int32_t *half_stop;         // [F] or null: park the frame after this half (serving epochs)
+  // serving: the launch decodes the frames named by a list (buffer indices;
+  // an entry -(f + 1) marks frame f as newly admitted: its counters are
+  // cleared and its status set to 255, "in progress"), each for at most
+  // epoch_halves halves; n_frames is then the list's length
+  int32_t *frame_list;        // [n_frames] or null: frames 0 .. n_frames-1, all new
+  int32_t epoch_halves;       // > 0 with frame_list and half_stop
+  int32_t grid_cap;           // > 0: at most this many blocks
 };
 
 // Mixed form: groups of frames, one code per group, in one launch.
