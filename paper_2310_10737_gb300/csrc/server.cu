@@ -59,7 +59,7 @@ struct Request {
   int32_t *half_iters = nullptr;
   uint8_t *status = nullptr;
   int64_t *queries = nullptr;
-  std::vector<int32_t> slots;
+  int32_t first = -1;  // the request's frames occupy slots first .. first + frames - 1
   int64_t remaining = 0;
   double t_submit = 0, t_done = 0;
   int state = 0;  // 0 waiting, 1 resident, 2 done
@@ -81,12 +81,45 @@ struct Pool {
   uint8_t *h_status = nullptr; // pinned [slots]
   int32_t *h_ctrl = nullptr;   // pinned [4]
   cudaStream_t stream = nullptr;
-  std::vector<int32_t> free_slots;
+  std::map<int32_t, int32_t> free_runs;  // free slot ranges: first -> length (coalesced)
+  int64_t free_count = 0;
   std::vector<int32_t> active;  // resident frames: slot, or -(slot + 1) for one admitted since the last launch
   std::vector<Request *> owner;  // [slots]
   std::deque<Request *> waiting;
   bool running = false;
   int64_t launched_words = 0;
+  // requests whose outputs are being copied out: done once the event has fired
+  std::vector<std::pair<cudaEvent_t, std::vector<Request *>>> draining;
+  std::vector<cudaEvent_t> spare_events;
+
+  // first-fit allocation of `len` consecutive slots; -1 if no run is long enough
+  int32_t alloc(int32_t len) {
+    for (auto it = free_runs.begin(); it != free_runs.end(); ++it) {
+      if (it->second < len) continue;
+      const int32_t first = it->first, rest = it->second - len;
+      free_runs.erase(it);
+      if (rest > 0) free_runs[first + len] = rest;
+      free_count -= len;
+      return first;
+    }
+    return -1;
+  }
+  void release(int32_t first, int32_t len) {
+    auto it = free_runs.emplace(first, len).first;
+    free_count += len;
+    auto nx = std::next(it);
+    if (nx != free_runs.end() && it->first + it->second == nx->first) {
+      it->second += nx->second;
+      free_runs.erase(nx);
+    }
+    if (it != free_runs.begin()) {
+      auto pv = std::prev(it);
+      if (pv->first + pv->second == it->first) {
+        pv->second += it->second;
+        free_runs.erase(it);
+      }
+    }
+  }
 };
 
 }  // namespace
@@ -142,8 +175,40 @@ size_t carve(Pool &p, int max_iter, char *mem) {
   return off;
 }
 
-// Retire the frames of pool p that finished in its last launch; completes
-// requests whose last frame finished (copies their outputs to host memory).
+// Requests whose output copies have completed are reported done.
+void finish_drained(sogrand_server *sv, Pool &p, bool wait) {
+  std::vector<Request *> done;
+  for (size_t i = 0; i < p.draining.size();) {
+    cudaEvent_t ev = p.draining[i].first;
+    const cudaError_t q = !ev ? cudaSuccess : (wait ? cudaEventSynchronize(ev) : cudaEventQuery(ev));
+    if (q == cudaErrorNotReady) {
+      i++;
+      continue;
+    }
+    for (Request *r : p.draining[i].second) {
+      if (q != cudaSuccess) r->rc = SOGRAND_ECUDA;
+      done.push_back(r);
+    }
+    if (ev) p.spare_events.push_back(ev);
+    p.draining.erase(p.draining.begin() + i);
+  }
+  if (done.empty()) return;
+  const double t = now_ms();
+  std::lock_guard<std::mutex> g(sv->mu);
+  for (Request *r : done) {
+    r->t_done = t;
+    r->state = 2;
+    sv->frames_done += r->frames;
+    sv->requests_done++;
+  }
+  sv->cv.notify_all();
+}
+
+// Retire the frames of pool p that stopped in its last launch.  A request
+// whose last frame stopped has its outputs (contiguous slots) copied to its
+// host buffers on the pool's stream; its slots are free at once (later work
+// on the stream runs after the copies), and it is reported done when the
+// copies have completed.
 void retire(sogrand_server *sv, Pool &p) {
   std::vector<int32_t> still;
   std::vector<Request *> completed;
@@ -163,47 +228,48 @@ void retire(sogrand_server *sv, Pool &p) {
   cudaError_t e = cudaSuccess;
   const size_t nb = ((size_t)p.n * p.n + 7) / 8;
   for (Request *r : completed) {
-    for (int64_t j = 0; j < r->frames && e == cudaSuccess; j++) {
-      const int32_t slot = r->slots[j];
-      e = cudaMemcpyAsync(r->bits + j * nb, p.bits + slot * nb, nb, cudaMemcpyDeviceToHost, p.stream);
-      if (e == cudaSuccess && r->half_iters)
-        e = cudaMemcpyAsync(r->half_iters + j, p.half_iters + slot, 4, cudaMemcpyDeviceToHost, p.stream);
-      if (e == cudaSuccess && r->status)
-        e = cudaMemcpyAsync(r->status + j, p.status + slot, 1, cudaMemcpyDeviceToHost, p.stream);
-      if (e == cudaSuccess && r->queries)
-        e = cudaMemcpyAsync(r->queries + j, p.queries + slot, 8, cudaMemcpyDeviceToHost, p.stream);
-    }
-  }
-  if (e == cudaSuccess) e = cudaStreamSynchronize(p.stream);
-  const double t = now_ms();
-  std::lock_guard<std::mutex> g(sv->mu);
-  for (Request *r : completed) {
-    for (int32_t slot : r->slots) {
-      p.owner[slot] = nullptr;
-      p.free_slots.push_back(slot);
-    }
-    r->t_done = t;
-    r->state = 2;
+    const size_t F = (size_t)r->frames, f0 = (size_t)r->first;
+    e = cudaMemcpyAsync(r->bits, p.bits + f0 * nb, F * nb, cudaMemcpyDeviceToHost, p.stream);
+    if (e == cudaSuccess && r->half_iters)
+      e = cudaMemcpyAsync(r->half_iters, p.half_iters + f0, F * 4, cudaMemcpyDeviceToHost, p.stream);
+    if (e == cudaSuccess && r->status)
+      e = cudaMemcpyAsync(r->status, p.status + f0, F, cudaMemcpyDeviceToHost, p.stream);
+    if (e == cudaSuccess && r->queries)
+      e = cudaMemcpyAsync(r->queries, p.queries + f0, F * 8, cudaMemcpyDeviceToHost, p.stream);
     r->rc = failed ? SOGRAND_ETIMEOUT : (e == cudaSuccess ? SOGRAND_OK : SOGRAND_ECUDA);
-    sv->frames_done += r->frames;
-    sv->requests_done++;
+    for (int64_t j = 0; j < r->frames; j++) p.owner[r->first + j] = nullptr;
   }
-  sv->cv.notify_all();
+  cudaEvent_t ev = nullptr;
+  if (!p.spare_events.empty()) {
+    ev = p.spare_events.back();
+    p.spare_events.pop_back();
+  } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    ev = nullptr;
+  }
+  if (ev && cudaEventRecord(ev, p.stream) == cudaSuccess) {
+    p.draining.emplace_back(ev, completed);
+  } else {  // no event: wait for the copies here
+    if (cudaStreamSynchronize(p.stream) != cudaSuccess)
+      for (Request *r : completed) r->rc = SOGRAND_ECUDA;
+    if (ev) p.spare_events.push_back(ev);
+    p.draining.emplace_back(nullptr, completed);
+  }
+  std::lock_guard<std::mutex> g(sv->mu);
+  for (Request *r : completed) p.release(r->first, (int32_t)r->frames);
 }
 
-// Admit waiting requests of pool p in arrival order while slots last; copy their LLRs in.
+// Admit waiting requests of pool p in arrival order while a run of free
+// slots is long enough; one copy of each request's LLRs into its slots.
 void admit(sogrand_server *sv, Pool &p) {
   std::vector<Request *> in;
   {
     std::lock_guard<std::mutex> g(sv->mu);
-    while (!p.waiting.empty() && (int64_t)p.free_slots.size() >= p.waiting.front()->frames) {
+    while (!p.waiting.empty()) {
       Request *r = p.waiting.front();
+      const int32_t first = p.alloc((int32_t)r->frames);
+      if (first < 0) break;
       p.waiting.pop_front();
-      r->slots.resize(r->frames);
-      for (int64_t j = 0; j < r->frames; j++) {
-        r->slots[j] = p.free_slots.back();
-        p.free_slots.pop_back();
-      }
+      r->first = first;
       r->remaining = r->frames;
       r->state = 1;
       in.push_back(r);
@@ -211,11 +277,11 @@ void admit(sogrand_server *sv, Pool &p) {
   }
   const size_t fb = (size_t)p.n * p.n * sizeof(float);
   for (Request *r : in) {
+    cudaMemcpyAsync((char *)p.llr + (size_t)r->first * fb, r->llr, (size_t)r->frames * fb, cudaMemcpyHostToDevice,
+                    p.stream);
     for (int64_t j = 0; j < r->frames; j++) {
-      const int32_t slot = r->slots[j];
-      cudaMemcpyAsync((char *)p.llr + slot * fb, (const char *)r->llr + j * fb, fb, cudaMemcpyHostToDevice, p.stream);
-      p.owner[slot] = r;
-      p.active.push_back(-slot - 1);
+      p.owner[r->first + j] = r;
+      p.active.push_back(-(r->first + (int32_t)j) - 1);
     }
   }
 }
@@ -265,6 +331,11 @@ void worker_main(sogrand_server *sv) {
     bool progress = false;
     for (auto &pp : sv->pools) {
       Pool &p = *pp;
+      if (!p.draining.empty()) {
+        const size_t before = p.draining.size();
+        finish_drained(sv, p, false);
+        progress = progress || p.draining.size() != before;
+      }
       if (p.running) {
         const cudaError_t q = cudaStreamQuery(p.stream);
         if (q == cudaErrorNotReady) continue;
@@ -297,7 +368,7 @@ void worker_main(sogrand_server *sv) {
     std::unique_lock<std::mutex> lk(sv->mu);
     bool busy = false, waiting = false;
     for (auto &pp : sv->pools) {
-      busy = busy || pp->running || !pp->active.empty();
+      busy = busy || pp->running || !pp->active.empty() || !pp->draining.empty();
       waiting = waiting || !pp->waiting.empty();
     }
     if (sv->stop && !busy && !waiting) return;
@@ -355,8 +426,8 @@ int sogrand_server_create(int n_codes, sogrand_code *const *codes, const int64_t
         cudaStreamCreateWithFlags(&p->stream, cudaStreamNonBlocking) != cudaSuccess) {
       rc = SOGRAND_ECUDA;
     }
-    p->free_slots.resize(p->slots);
-    for (int64_t j = 0; j < p->slots; j++) p->free_slots[j] = (int32_t)(p->slots - 1 - j);
+    p->free_runs[0] = (int32_t)p->slots;
+    p->free_count = p->slots;
     p->owner.assign(p->slots, nullptr);
     sv->pools.push_back(std::move(p));
   }
@@ -419,7 +490,7 @@ int sogrand_server_stats(sogrand_server *sv, int64_t *launches, int64_t *frames_
   std::lock_guard<std::mutex> g(sv->mu);
   int64_t res = 0, wait = 0;
   for (auto &p : sv->pools) {
-    res += (int64_t)(p->slots - (int64_t)p->free_slots.size());
+    res += p->slots - p->free_count;
     wait += (int64_t)p->waiting.size();
   }
   if (launches) *launches = sv->launches;
@@ -443,6 +514,9 @@ int sogrand_server_destroy(sogrand_server *sv) {
       cudaStreamSynchronize(p->stream);
       cudaStreamDestroy(p->stream);
     }
+    for (auto &d : p->draining)
+      if (d.first) cudaEventDestroy(d.first);
+    for (cudaEvent_t ev : p->spare_events) cudaEventDestroy(ev);
     if (p->mem) cudaFree(p->mem);
     if (p->h_list) cudaFreeHost(p->h_list);
     if (p->h_status) cudaFreeHost(p->h_status);
