@@ -166,6 +166,105 @@ def job_rate(world, frames, info_bits_per_frame, steps, ms):
     return world * frames * info_bits_per_frame * steps / (ms / 1000)
 
 
+SERVE_CODES = ["ebch_32_26", "ebch_64_57", "ebch_64_51", "ebch_128_120"]
+
+
+def serving_bench(sg, torch, n_req, loads, seed, epoch_halves=2):
+    """Poisson arrivals of decode requests (code uniform over four eBCH product
+    codes, 1..64 frames, Eb/N0 uniform in 2.5..4 dB per request) into the
+    continuous-batching server, at several offered loads; and the same arrivals
+    decoded one request at a time (per-request launches of the plain form).
+    Latency = submission (arrival) to outputs in host memory."""
+    import threading
+    from workloads import awgn_frames, ebch
+    rng = np.random.default_rng(seed)
+    lin = [ebch(nm) for nm in SERVE_CODES]
+    codes = [sg.Code.from_linear_code(c) for c in lin]
+    t0 = time.perf_counter()
+    spec = [(int(rng.integers(0, len(lin))), int(rng.integers(1, 65)), float(rng.uniform(2.5, 4.0)))
+            for _ in range(n_req)]
+    # per code, every frame its requests need in one seeded batch (per-frame Eb/N0), then sliced
+    frames = {}
+    for ci, lc in enumerate(lin):
+        snr = np.concatenate([[e] * F for c, F, e in spec if c == ci] or [[3.0]])
+        frames[ci] = awgn_frames(lc, len(snr), snr, seed=seed, stream=100 + ci, threads=16)[2]
+    pos = [0] * len(lin)
+    reqs = []
+    for ci, F, _ in spec:
+        n = lin[ci].n
+        llr = torch.from_numpy(np.ascontiguousarray(frames[ci][pos[ci]:pos[ci] + F])).pin_memory()
+        pos[ci] += F
+        out = dict(bits=torch.empty((F, n * n // 8), dtype=torch.uint8, pin_memory=True),
+                   half_iters=torch.empty(F, dtype=torch.int32, pin_memory=True),
+                   status=torch.empty(F, dtype=torch.uint8, pin_memory=True),
+                   queries=torch.empty(F, dtype=torch.int64, pin_memory=True))
+        reqs.append((ci, llr, out, F * lin[ci].k ** 2))
+    del frames
+    log(f"serving: {n_req} requests ({sum(F for _, F, _ in spec)} frames) generated in {time.perf_counter() - t0:.1f} s")
+    for c, lc in zip(codes, lin):  # schedules tuned on a sample of that code's frames
+        _, _, smp = awgn_frames(lc, 2000, 3.0, seed=seed + 7)
+        c.tune(torch.from_numpy(smp).cuda(), L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER)
+    slots = [8192, 4096, 4096, 2048]
+    bits = sum(b for *_, b in reqs)
+    res = {"workload": "requests: code uniform over eBCH(32,26)^2, (64,57)^2, (64,51)^2, (128,120)^2; frames "
+                       "uniform 1..64; Eb/N0 uniform 2.5..4.0 dB per request; Poisson arrivals; L=4, cap 1e4, "
+                       "alpha 0.5, max 20 iterations",
+           "requests": n_req, "info_bits": bits, "epoch_halves": epoch_halves,
+           "slots": dict(zip(SERVE_CODES, slots)), "latency": "submission to outputs in host memory",
+           "server": [], "per_request_plain": []}
+
+    def pct(v, q):
+        return float(np.percentile(np.array(v), q)) if v else None
+
+    for lam in loads:
+        gaps = rng.exponential(1.0 / lam, n_req)
+        arrive = np.cumsum(gaps) - gaps[0]
+        srv = sg.Server(codes, slots, L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER,
+                        epoch_halves=epoch_halves)
+        tickets = [None] * n_req
+
+        def client():
+            start = time.perf_counter()
+            for i, (ci, llr, out, _) in enumerate(reqs):
+                d = start + arrive[i] - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                tickets[i] = srv.submit(ci, llr, out)[0]
+
+        t_start = time.perf_counter()
+        th = threading.Thread(target=client)
+        th.start()
+        th.join()
+        lat = [srv.wait(t, timeout_ms=600000)[1] for t in tickets]
+        span = time.perf_counter() - t_start
+        st = srv.stats()
+        srv.close()
+        res["server"].append({"offered_rps": lam, "achieved_rps": n_req / span, "p50_ms": pct(lat, 50),
+                              "p99_ms": pct(lat, 99), "bits_per_s": bits / span, "launches": st["launches"]})
+        log(f"serving: server at {lam:g} req/s: p50 {pct(lat, 50):.2f} ms p99 {pct(lat, 99):.2f} ms, "
+            f"{bits / span:.3e} bits/s, {st['launches']} launches")
+        # the same arrivals served one request at a time, plain form (one launch per half)
+        lat = []
+        start = time.perf_counter()
+        for i, (ci, llr, _, _) in enumerate(reqs):
+            a = start + arrive[i]
+            d = a - time.perf_counter()
+            if d > 0:
+                time.sleep(d)
+            o = sg.product_decode(codes[ci], llr.cuda(non_blocking=True), L=L_LIST, query_cap=CAP, alpha=ALPHA,
+                                  max_iter=MAX_ITER, persistent=False, stats=False)
+            o["bits"].cpu()
+            lat.append(1000 * (time.perf_counter() - a))
+        span = time.perf_counter() - start
+        res["per_request_plain"].append({"offered_rps": lam, "achieved_rps": n_req / span, "p50_ms": pct(lat, 50),
+                                         "p99_ms": pct(lat, 99), "bits_per_s": bits / span})
+        log(f"serving: per-request plain at {lam:g} req/s: p50 {pct(lat, 50):.2f} ms p99 {pct(lat, 99):.2f} ms, "
+            f"{bits / span:.3e} bits/s")
+    for c in codes:
+        c.close()
+    return res
+
+
 def cpu_oracle_rate(code, lch, threads):
     """The oracle (FP64, plain C, all host cores) on a bounded sample: info bits/s."""
     import oracle
@@ -217,6 +316,8 @@ def main():
     ap.add_argument("--form", default="persistent", choices=["persistent", "plain"],
                     help="persistent: one kernel per decode with a device-side frame queue; plain: one launch per half")
     ap.add_argument("--plain-steps", type=int, default=3, help="steps of the other form, timed for comparison (0: off)")
+    ap.add_argument("--serve-requests", type=int, default=1200, help="requests per offered load in the serving run (0: off)")
+    ap.add_argument("--serve-loads", default="250,500,1000,2000", help="offered loads, requests/s")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -264,13 +365,17 @@ def main():
                                  persistent=persistent)
 
     def timed(persistent, steps, warmup, sample_clocks):
+        # the clock sampler starts before the warm-up steps, and the warm-up steps
+        # do the timed steps' work (the first per-step reduction loads torch's
+        # kernel, about a second): nothing one-off stays in the timed region
+        clocks = ClockSampler() if sample_clocks else None
         for i in range(warmup):
             t0 = time.perf_counter()
             step(persistent)
+            int(out["queries"].sum().item())
             torch.cuda.synchronize()
             log(f"{'persistent' if persistent else 'plain'} warm-up step {i}: {1000 * (time.perf_counter() - t0):.1f} ms")
         out["weight_sum"].zero_()
-        clocks = ClockSampler() if sample_clocks else None
         if clocks:
             clocks.mark()
         if dist:
@@ -282,14 +387,18 @@ def main():
         t_kern = t_check = 0.0
         launches = kern_launches = 0
         qtot = 0
+        walls = []
         for _ in range(steps):
+            tw = time.perf_counter()
             o = step(persistent)
             t_kern += o["timing_ms"][0]
             t_check += o["timing_ms"][1]
             launches += o["launches"]
             kern_launches += 1 if persistent else o["launches"] // 2
             qtot += int(out["queries"].sum().item())
+            walls.append((round(1000 * (time.perf_counter() - tw), 1), round(o["timing_ms"][0], 1)))
         ev1.record(stream)
+        log(f"{'persistent' if persistent else 'plain'} steps (wall ms, kernel ms): {walls}")
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
@@ -366,6 +475,11 @@ def main():
                                "iterations": float(hi[sel].mean() / 2), "queries_per_bit": float(qf[sel].mean() / (n * n)),
                                "par_queries_per_bit": float(pq[sel].mean() / (n * n))}
 
+    serving = None
+    if rank == 0 and args.serve_requests > 0:
+        serving = serving_bench(sg, torch, args.serve_requests, [float(x) for x in args.serve_loads.split(",")],
+                                SEED + 1000 + rank)
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_frames > 0:
         rate, dt = cpu_oracle_rate(code, lch[: args.cpu_frames], cores)
@@ -380,7 +494,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(F),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "queries_per_s": world * qtot / (ms / 1000), "xf_words": int(out["xf_words"].item()),
-                "quality": quality,
+                "quality": quality, "serving": serving,
                 "schedule": {"blocks_per_sm": sched, "tuned_on": f"{min(F, 10_000)} frames",
                              "sample_ms": {"6": sched_ms[0], "8": sched_ms[1]}},
                 "form": ("persistent (one kernel per decode, device-side frame queue)" if main_persistent
