@@ -44,8 +44,8 @@ METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 # capture of a 10,000-frame decode of this workload (traffic grows with the
 # frame count at a fixed Eb/N0 mix), valid only for the kernel sources whose
 # digest is recorded with it: `traffic` is null once they change.
-TRAFFIC = {"csrc_digest": "e62829059c3264b3ae2bd09ca1401a8f7e4e7096d808b78806ca63e471c9c00b",
-           "bytes_per_frame": 262192.0,
+TRAFFIC = {"csrc_digest": "c1534a7486cbb5ee114116484534463776c9921b07ebbdb74f4a441a67c9ede7",
+           "bytes_per_frame": 313932.0,
            "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md"}
 
 
