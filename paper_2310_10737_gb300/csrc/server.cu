@@ -145,14 +145,14 @@ struct sogrand_server {
 
 namespace {
 
-size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
+size_t round256(size_t x) { return (x + 255) & ~size_t(255); }
 
 // Carve one pool's device arrays out of `mem` (or just count the bytes).
 size_t carve(Pool &p, int max_iter, char *mem) {
   size_t off = 0;
   auto take = [&](size_t b) {
     char *r = mem ? mem + off : nullptr;
-    off += al256(b);
+    off += round256(b);
     return r;
   };
   const size_t S = (size_t)p.slots;
