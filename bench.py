@@ -44,18 +44,21 @@ METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 # capture of a 10,000-frame decode of this workload (traffic grows with the
 # frame count at a fixed Eb/N0 mix), valid only for the kernel sources whose
 # digest is recorded with it: `traffic` is null once they change.
-TRAFFIC = {"csrc_digest": "c1534a7486cbb5ee114116484534463776c9921b07ebbdb74f4a441a67c9ede7",
+TRAFFIC = {"csrc_digest": "6f46b90f6c6c4ba32d3f8979e2e4a073612b9823ec0092015169bd72908b4666",
            "bytes_per_frame": 313932.0,
            "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md"}
 
 
+KERNEL_SOURCES = ("kernels.cuh", "launch.h", "sg_common.h", "siso_warp.cuh")  # what k_product_persistent compiles from
+
+
 def csrc_digest():
-    """SHA-256 of the CUDA sources (profiling-only #ifdef SG_PHASE_PROFILE blocks left out)."""
+    """SHA-256 of the measured kernel's sources (profiling-only #ifdef SG_PHASE_PROFILE blocks left out)."""
     import hashlib
     d = os.path.join(ROOT, "paper_2310_10737_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(d)):
-        if not name.endswith((".cu", ".cuh", ".h")):
+        if name not in KERNEL_SOURCES:
             continue
         keep, depth = [], 0
         for line in open(os.path.join(d, name)):
