@@ -112,6 +112,21 @@ int sogrand_decode(sogrand_code *code, int64_t n_words, const float *llr_ch, con
                    int64_t *queries, uint64_t *list_words, float *list_app, int32_t *list_count, void *stream);
 
 /*
+ * The same SISO decoding with Forney's approximation of the soft output
+ * (Sec. IV, eq. missingterm): the APPs are normalised over the list alone, the
+ * mass of the codewords outside the list being taken as 0.  The paper uses it
+ * as the comparison for SOGRAND's soft output (Fig. list_BLER: Forney's
+ * predicted list-BLER for the first L' words of an (L'+1)-word list is the
+ * last word's APP).  Outputs as sogrand_decode, with p_miss = 0 and
+ * L_APP = +-infinity for bits on which every listed word agrees; an empty list
+ * gives L_APP = lambda and p_miss = 1.  There is no threshold rule (its
+ * prediction would always be 0).  Errors: EINVAL, ENOMEM, ECUDA.
+ */
+int sogrand_decode_forney(sogrand_code *code, int64_t n_words, const float *llr_ch, const float *llr_a, int L,
+                          int64_t query_cap, uint8_t *hard, float *llr_app, float *llr_ext, float *p_miss,
+                          int64_t *queries, uint64_t *list_words, float *list_app, int32_t *list_count, void *stream);
+
+/*
  * Block turbo decoding of n_frames product codes (Sec. VI, Fig. turboDec):
  * L_A = 0; each half iteration decodes every row (odd halves) or column (even
  * halves) of every running frame with SOGRAND (lambda = L_Ch + fl32(alpha L_E)

@@ -59,7 +59,11 @@ def _ptr(a):
 
 
 class OracleCode:
-    """Oracle view of a linear code: H plus the even/reading/c_max options."""
+    """Oracle view of a linear code: H plus the even/reading/c_max options.
+
+    reading 0: the parity-class normalisation (reading B); 1: the literal one
+    (reading A); 2: Forney's approximation, APPs normalised over the list.
+    """
 
     def __init__(self, code, even: bool | None = None, reading: int = 0, c_max: int | None = None):
         self.code = code

@@ -51,7 +51,9 @@ typedef struct {
     int k;
     const uint8_t *H; /* (n-k) x n, row-major, entries 0/1 */
     int even;         /* 1: even code, parity skip (Sec. III-B) */
-    int reading;      /* 0: reading B (parity class); 1: reading A (literal) */
+    int reading;      /* 0: reading B (parity class); 1: reading A (literal);
+                         2: Forney's approximation (eq. missingterm): reading B's
+                         search, the mass outside the list taken as 0 */
     int c_max;        /* clamp of the 1-line parameter */
 } oracle_code;
 
@@ -375,7 +377,7 @@ static int siso_emit(void *vctx, const int *ranks, int w, int64_t cost)
         s->hit_logp[h] = lp;
         s->hit_q[h] = s->q;
         if (s->nhit >= s->L) return 1;
-        if (s->thr > 0) {
+        if (s->thr > 0 && s->code->reading != 2) { /* Forney's prediction is always 0: no threshold */
             double M = remaining_log(s, s->cur_C, s->cur_idx) + s->logphi;
             if (pmiss_of(s->hit_logp, s->nhit, M) < s->thr) {
                 s->stop_thr = 1;
@@ -461,7 +463,7 @@ int oracle_siso(const oracle_code *code, const float *lch, const float *la, int 
     }
     s->c = oracle_one_line_c(n, absf, code->c_max);
     s->cls = code->even ? par : -1;
-    if (code->even && code->reading == 0) s->logphi = log_pow2m1(k) - log_pow2m1(n - 1);
+    if (code->even && code->reading != 1) s->logphi = log_pow2m1(k) - log_pow2m1(n - 1);
     else s->logphi = log_pow2m1(k) - log_pow2m1(n);
     s->cur_C = -1;
     int stopped = gen_all(n, s->c, s->cls, siso_emit, s);
@@ -475,6 +477,7 @@ int oracle_siso(const oracle_code *code, const float *lch, const float *la, int 
             logR = logadd(tail[s->cls ^ 1], head[s->cls ^ 1]);
         } else logR = -INFINITY;
     } else logR = remaining_log(s, s->cur_C, s->cur_idx);
+    if (code->reading == 2) logR = -INFINITY; /* Forney: nothing outside the list */
 
     /* paper-literal remaining mass: (class total) - S, FP64 */
     double tp = 1, tm = 1;

@@ -9,7 +9,8 @@ Public entry points (same names as the C ABI in include/sogrand.h):
 * :class:`Server` -- continuous-batching decode service (requests admitted as slots free up);
 * :func:`sogrand_trace_patterns` -- the device's canonical query order (test hook);
 * :func:`sogrand_release_cached` -- hand the decoders' pooled scratch back to the device;
-* :func:`sogrand_int_peak` -- the measured integer-pipe rate (the roofline's denominator).
+* :func:`sogrand_int_peak` -- the measured integer-pipe rate (the roofline's denominator);
+* :mod:`calibration` -- predicted vs empirical list-BLER and BER (SOGRAND and Forney's approximation).
 
 All compute runs in hand-written CUDA kernels for sm_103a (libsogrand.so);
 PyTorch only provides device memory and streams.

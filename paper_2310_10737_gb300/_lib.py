@@ -57,6 +57,7 @@ def load() -> C.CDLL:
         L.sogrand_code_reserve.argtypes = [vp, i64]
         L.sogrand_code_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.sogrand_decode.argtypes = [vp, i64, vp, vp, i32, i64, f32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
+        L.sogrand_decode_forney.argtypes = [vp, i64, vp, vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.product_decode.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp]
         L.product_decode_ex.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp,
                                         C.POINTER(ProductStats), vp]
@@ -80,6 +81,7 @@ def load() -> C.CDLL:
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
+                     "sogrand_decode_forney",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
                      "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak",
                      "product_decode_mixed", "sogrand_code_schedule", "sogrand_code_tune", "sogrand_server_create",
@@ -170,8 +172,9 @@ def sogrand_code_create(H, even: bool = True) -> Code:
 
 
 def sogrand_decode(code: Code, llr_ch, llr_a=None, L: int = 4, query_cap: int = 10**4, thr: float = 0.0,
-                   lists: bool = True, stream=None) -> dict:
-    """Decode the rows of ``llr_ch`` ([W, n] float32 CUDA tensor); returns CUDA tensors."""
+                   lists: bool = True, stream=None, forney: bool = False) -> dict:
+    """Decode the rows of ``llr_ch`` ([W, n] float32 CUDA tensor); returns CUDA tensors.
+    forney=True: Forney's list-only normalisation (sogrand_decode_forney)."""
     import torch
     W, n = llr_ch.shape
     assert n == code.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
@@ -188,11 +191,15 @@ def sogrand_decode(code: Code, llr_ch, llr_a=None, L: int = 4, query_cap: int = 
         out.update(list_words=torch.empty((W, L, nm), dtype=torch.int64, device=dev),
                    list_app=torch.empty((W, L), dtype=torch.float32, device=dev),
                    list_count=torch.empty(W, dtype=torch.int32, device=dev))
-    rc = load().sogrand_decode(code.handle, W, _ptr(llr_ch), _ptr(llr_a), int(L), int(query_cap), float(thr),
-                               _ptr(out["hard"]), _ptr(out["llr_app"]), _ptr(out["llr_ext"]), _ptr(out["p_miss"]),
-                               _ptr(out["queries"]), _ptr(out.get("list_words")), _ptr(out.get("list_app")),
-                               _ptr(out.get("list_count")), _stream(stream))
-    _check(rc, "sogrand_decode")
+    tail = (_ptr(out["hard"]), _ptr(out["llr_app"]), _ptr(out["llr_ext"]), _ptr(out["p_miss"]), _ptr(out["queries"]),
+            _ptr(out.get("list_words")), _ptr(out.get("list_app")), _ptr(out.get("list_count")), _stream(stream))
+    if forney:
+        assert thr == 0.0, "Forney's normalisation has no threshold rule"
+        rc = load().sogrand_decode_forney(code.handle, W, _ptr(llr_ch), _ptr(llr_a), int(L), int(query_cap), *tail)
+    else:
+        rc = load().sogrand_decode(code.handle, W, _ptr(llr_ch), _ptr(llr_a), int(L), int(query_cap), float(thr),
+                                   *tail)
+    _check(rc, "sogrand_decode_forney" if forney else "sogrand_decode")
     return out
 
 

@@ -472,22 +472,43 @@ int sogrand_code_info(const sogrand_code *c, int *n, int *k) {
   return SOGRAND_OK;
 }
 
-int sogrand_decode(sogrand_code *c, int64_t n_words, const float *llr_ch, const float *llr_a, int L, int64_t cap,
-                   float thr, uint8_t *hard, float *llr_app, float *llr_ext, float *p_miss, int64_t *queries,
-                   uint64_t *list_words, float *list_app, int32_t *list_count, void *stream) {
-  if (!c || n_words < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f))
+}  // extern "C"
+
+namespace {
+int decode_words(sogrand_code *c, int64_t n_words, const float *llr_ch, const float *llr_a, int L, int64_t cap,
+                 float thr, int forney, uint8_t *hard, float *llr_app, float *llr_ext, float *p_miss, int64_t *queries,
+                 uint64_t *list_words, float *list_app, int32_t *list_count, void *stream) {
+  if (!c || n_words < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f) ||
+      (forney && thr > 0.f))
     return SOGRAND_EINVAL;
   if (n_words > 0 && !llr_ch) return SOGRAND_EINVAL;
   if (n_words == 0) return SOGRAND_OK;
   int rc = ensure_cap(c, cap);
   if (rc != SOGRAND_OK) return rc;
   sg::DevCode d = dev_code(c);
-  sg::SisoParams P{L, (int32_t)cap, thr};
+  sg::SisoParams P{L, (int32_t)cap, thr, forney};
   sg::DecodeArgs a{n_words, llr_ch, llr_a, hard, llr_app, llr_ext, p_miss, queries, list_words, list_app, list_count,
                    nullptr};
   cudaError_t e;
   SG_DISPATCH(c, e = (sg::launch_decode<NPL, SYN>(d, P, a, (cudaStream_t)stream)));
   return e == cudaSuccess ? SOGRAND_OK : SOGRAND_ECUDA;
+}
+}  // namespace
+
+extern "C" {
+
+int sogrand_decode(sogrand_code *c, int64_t n_words, const float *llr_ch, const float *llr_a, int L, int64_t cap,
+                   float thr, uint8_t *hard, float *llr_app, float *llr_ext, float *p_miss, int64_t *queries,
+                   uint64_t *list_words, float *list_app, int32_t *list_count, void *stream) {
+  return decode_words(c, n_words, llr_ch, llr_a, L, cap, thr, 0, hard, llr_app, llr_ext, p_miss, queries, list_words,
+                      list_app, list_count, stream);
+}
+
+int sogrand_decode_forney(sogrand_code *c, int64_t n_words, const float *llr_ch, const float *llr_a, int L,
+                          int64_t cap, uint8_t *hard, float *llr_app, float *llr_ext, float *p_miss, int64_t *queries,
+                          uint64_t *list_words, float *list_app, int32_t *list_count, void *stream) {
+  return decode_words(c, n_words, llr_ch, llr_a, L, cap, 0.f, 1, hard, llr_app, llr_ext, p_miss, queries, list_words,
+                      list_app, list_count, stream);
 }
 
 int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L, int64_t cap,

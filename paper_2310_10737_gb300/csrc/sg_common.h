@@ -44,6 +44,7 @@ struct SisoParams {
   int32_t L;
   int32_t cap;
   float thr;
+  int32_t forney;  // 1: Forney's list-only normalisation (the mass outside the list taken as 0)
 };
 
 // Per-word results that the callers write out.

@@ -1084,7 +1084,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
 
   // soft output (Corollary + eq. LLRi)
   if (!have_lr2)
-    lr2 = exhausted ? -CUDART_INF_F
+    lr2 = (exhausted || P.forney) ? -CUDART_INF_F
                     : remaining_log2<NPL, SYN>(sc, O, tb, tc, q - 1, n, h.c, cls, lane, df_warp_sum(tmass),
                                                flags);
 #ifdef SG_PHASE_PROFILE

@@ -1,0 +1,82 @@
+"""Soft-output calibration on the GPU (Sec. IV, Fig. list_BLER; Sec. V bitwise SO).
+
+eBCH(64,57) words at Eb/N0 = 2 dB, the paper's setting: SOGRAND's predicted
+list-BLER (L = 4) must match the empirical list-BLER in every populated bin
+within its counting error, while Forney's approximation (L = 5) predicts far
+fewer misses than occur, as the paper's figure shows (its points are in
+tests/golden/list_bler_calibration_ebch64_57.txt).  The bitwise prediction
+1/(1+e^|L_APP|) must match the observed bit-error rate as well.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+
+from workloads import awgn_words, ebch
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "list_bler_calibration_ebch64_57.txt")
+
+
+@pytest.fixture(scope="module")
+def run():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_2310_10737_gb300 as sg
+    from paper_2310_10737_gb300 import calibration
+    lc = ebch("ebch_64_57")
+    _, X, L = awgn_words(lc, 200_000, 2.0, seed=4242, threads=16)
+    c = sg.Code.from_linear_code(lc)
+    llr = torch.from_numpy(L).cuda()
+    res = calibration.list_bler_calibration(c, llr, X, L=4)
+    bits = calibration.bit_calibration(c, llr, X, L=4)
+    bits_f = calibration.bit_calibration(c, llr, X, L=4, forney=True)
+    c.close()
+    return res, bits, bits_f
+
+
+def _paper(method):
+    pts = [ln.split() for ln in open(GOLDEN) if ln.strip() and not ln.startswith("#")]
+    return [(float(p), float(e)) for m, p, e in pts if m == method]
+
+
+def test_sogrand_list_bler_is_calibrated(run):
+    res, _, _ = run
+    rows = res["sogrand"]
+    assert len(rows) >= 5
+    for r in rows:
+        expect, got = r["expected_errors"], r["errors"]
+        assert abs(got - expect) < 4.5 * math.sqrt(max(expect, 1.0)) + 0.1 * expect, r
+    # the paper's points lie on the same line (empirical / predicted between 0.8 and 1.0)
+    for p, e in _paper("sogrand"):
+        assert 0.75 < e / p < 1.05
+
+
+def test_forney_underestimates_the_list_bler(run):
+    res, _, _ = run
+    low = [r for r in res["forney"] if r["predicted"] < 0.03 and r["lo"] > 0]
+    assert len(low) >= 3
+    for r in low:
+        assert r["empirical"] > 3.0 * r["predicted"], r
+    for p, e in _paper("forney"):  # the paper's points: 5 to 120 times the prediction
+        assert e / p > 5.0
+    pred_s, miss_s = res["overall"]["sogrand"]
+    pred_f, miss_f = res["overall"]["forney"]
+    assert abs(miss_s - pred_s) < 0.05 * miss_s and pred_f < 0.5 * miss_f
+
+
+def test_bitwise_prediction(run):
+    _, bits, bits_f = run
+    assert len(bits) >= 5
+    for r in bits:
+        expect, got = r["expected_errors"], r["errors"]
+        assert abs(got - expect) < 4.5 * math.sqrt(max(expect, 1.0)) + 0.15 * expect, r
+    # Forney's infinite L_APPs (predicted error 0) are wrong far more often than predicted
+    first = bits_f[0]
+    assert first["lo"] == 0.0
+    assert first["errors"] > first["expected_errors"] + 4.5 * math.sqrt(max(first["expected_errors"], 1.0))

@@ -161,3 +161,22 @@ def test_trace_order_matches_oracle(env, oracle_lib):
             par = int((lam < 0).sum() & 1)
             ranks, _, _ = oracle_lib.trace(n, cdev, par, 3000)
             np.testing.assert_array_equal(masks, ranks, err_msg=f"{name} trial {trial}")
+
+
+@pytest.mark.parametrize("name,ebn0,W,L", [("ebch_16_11", 2.0, 700, 5), ("ebch_32_26", 2.0, 1500, 5),
+                                           ("ebch_64_57", 2.0, 1200, 5), ("ebch_64_51", 3.0, 400, 2),
+                                           ("ebch_128_120", 4.0, 300, 1)])
+def test_forney_parity(env, oracle_lib, name, ebn0, W, L):
+    """Forney's list-only normalisation (eq. missingterm) against the oracle's
+    reading 2: same search, APPs over the list, infinite L_APP on unanimous bits."""
+    torch, sg, get = env
+    lc, c, _ = get(name)
+    _, _, lch = awgn_words(lc, W, ebn0, seed=2000 + W)
+    out = sg.sogrand_decode(c, torch.from_numpy(lch).cuda(), L=L, query_cap=10**4, forney=True)
+    torch.cuda.synchronize()
+    ref = oracle_lib.siso_batch(oracle_lib.OracleCode(lc, reading=2), lch, L=L, cap=10**4)
+    compare_siso(lc, out, ref, f"Forney {name} {ebn0}dB L={L}")
+    pm = out["p_miss"].cpu().numpy()
+    cnt = out["list_count"].cpu().numpy()
+    assert (pm[cnt > 0] == 0).all() and (pm[cnt == 0] == 1).all()
+    assert sg._lib.load().sogrand_decode_forney(c.handle, 1, None, None, 4, 10, *([None] * 8), None) == 1  # EINVAL

@@ -237,3 +237,48 @@ def test_list_miss_probability_is_calibrated(oracle_lib):
     assert abs(miss.sum() - pred.sum()) < 4.5 * math.sqrt(pred.sum()) + 0.05 * pred.sum()
     pred_a, miss_a = _calibration(oracle_lib, 1, 4000)
     assert pred_a.sum() > 1.5 * miss_a.sum()
+
+
+@pytest.mark.parametrize("name,ebn0", [("ebch_8_4", 1.0), ("ebch_16_11", 2.0)])
+def test_forney_reading_with_the_whole_codebook_is_exact(oracle_lib, name, ebn0):
+    """Forney's approximation (eq. missingterm) drops the mass outside the
+    list; when the list holds the whole codebook nothing is dropped and the
+    APPs are the exact posterior (eq. formula:forney)."""
+    code = ebch(name)
+    oc = oracle_lib.OracleCode(code, reading=2)
+    book = _codebook(code)
+    _, X, L = awgn_words(code, 8, ebn0, seed=31)
+    for i in range(L.shape[0]):
+        r = oracle_lib.siso(oc, L[i], L=2 ** code.k + 1, cap=2 ** (code.n - 1))
+        lam = L[i].astype(np.float64)
+        assert r["list_count"] == 2 ** code.k and r["pmiss"] == 0.0
+        exact, ml = _exact_bitwise_llr(lam, book)
+        np.testing.assert_allclose(r["lapp"], exact, rtol=1e-10, atol=1e-10)
+        assert tuple(r["list_words"][np.argmax(r["list_app"])]) == tuple(ml)
+
+
+def test_forney_reading_normalises_over_the_list(oracle_lib):
+    code = ebch("ebch_32_26")
+    oc_f = oracle_lib.OracleCode(code, reading=2)
+    oc_b = oracle_lib.OracleCode(code)
+    _, X, L = awgn_words(code, 30, 2.0, seed=32)
+    for i in range(30):
+        f = oracle_lib.siso(oc_f, L[i], L=4, cap=10**4)
+        b = oracle_lib.siso(oc_b, L[i], L=4, cap=10**4)
+        # the same search: same list, same queries
+        assert f["queries"] == b["queries"] and f["list_count"] == b["list_count"]
+        if f["list_count"] == 0:
+            continue
+        assert f["pmiss"] == 0.0
+        assert abs(f["list_app"].sum() - 1.0) < 1e-12
+        # each Forney APP is SOGRAND's APP rescaled by 1 / (1 - P(miss))
+        np.testing.assert_allclose(f["list_app"], b["list_app"] / (1.0 - b["pmiss"]), rtol=1e-9)
+        # a bit on which every listed word agrees gets an infinite L_APP of that sign
+        W = f["list_words"]
+        unanimous = (W == W[0]).all(axis=0)
+        assert np.isinf(f["lapp"][unanimous]).all()
+        assert ((f["lapp"][unanimous] < 0) == (W[0][unanimous] == 1)).all()
+        assert np.isfinite(f["lapp"][~unanimous]).all()
+    f1 = oracle_lib.siso(oc_f, L[0], L=1, cap=10**4)
+    if f1["list_count"] == 1:
+        assert f1["list_app"][0] == 1.0
