@@ -50,6 +50,10 @@ def lib():
             L.oracle_product.argtypes = [C.POINTER(_Code), C.c_void_p, C.c_int, C.c_int64, C.c_double, C.c_float,
                                          C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
             L.oracle_product.restype = C.c_int
+            L.oracle_product2.argtypes = [C.POINTER(_Code), C.POINTER(_Code), C.c_void_p, C.c_int, C.c_int64,
+                                          C.c_double, C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_void_p, C.c_void_p]
+            L.oracle_product2.restype = C.c_int
             _lib = L
     return _lib
 
@@ -138,27 +142,31 @@ def siso_batch(oc: OracleCode, lch, la=None, L=4, cap=10**4, thr=0.0, threads=No
                 list_count=np.array([r["list_count"] for r in res], np.int32), items=res)
 
 
-def product(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20) -> dict:
-    n = oc.n
-    lch = np.ascontiguousarray(lch, dtype=np.float32).reshape(n * n)
-    bits = np.zeros(n * n, np.uint8)
+def product(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20, col: OracleCode | None = None) -> dict:
+    """One frame (row-major [n_col, n_row]) of the product of the row code `oc`
+    and the column code `col` (default: `oc`, a square product code)."""
+    col = oc if col is None else col
+    nr, nc = oc.n, col.n
+    lch = np.ascontiguousarray(lch, dtype=np.float32).reshape(nr * nc)
+    bits = np.zeros(nr * nc, np.uint8)
     hi = np.zeros(1, np.int32)
     st = np.zeros(1, np.uint8)
     q = np.zeros(1, np.int64)
     qp = np.zeros(1, np.int64)
-    lib().oracle_product(C.byref(oc._s), _ptr(lch), L, cap, thr, C.c_float(alpha), max_iter, _ptr(bits), _ptr(hi),
-                         _ptr(st), _ptr(q), _ptr(qp))
-    return dict(bits=bits.reshape(n, n), half_iters=int(hi[0]), status=int(st[0]), queries=int(q[0]),
+    lib().oracle_product2(C.byref(oc._s), C.byref(col._s), _ptr(lch), L, cap, thr, C.c_float(alpha), max_iter,
+                          _ptr(bits), _ptr(hi), _ptr(st), _ptr(q), _ptr(qp))
+    return dict(bits=bits.reshape(nc, nr), half_iters=int(hi[0]), status=int(st[0]), queries=int(q[0]),
                 par_queries=int(qp[0]))
 
 
-def product_batch(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20, threads=None) -> dict:
+def product_batch(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20, threads=None,
+                  col: OracleCode | None = None) -> dict:
     lch = np.ascontiguousarray(lch, dtype=np.float32)
     F = lch.shape[0]
     res = [None] * F
 
     def one(i):
-        res[i] = product(oc, lch[i], L, cap, thr, alpha, max_iter)
+        res[i] = product(oc, lch[i], L, cap, thr, alpha, max_iter, col)
 
     with ThreadPoolExecutor(_threads(threads)) as ex:
         list(ex.map(one, range(F)))

@@ -546,14 +546,15 @@ int oracle_siso(const oracle_code *code, const float *lch, const float *la, int 
 /* ------------------------------------------------------------------ */
 /* product codes: block turbo decoding (Sec. VI, Fig. turboDec)         */
 /* ------------------------------------------------------------------ */
-static int frame_valid(const oracle_code *code, const uint8_t *B, uint8_t *tmp)
+/* every row of the n_col x n_row frame is a row-code word and every column a column-code word */
+static int frame_valid(const oracle_code *row, const oracle_code *col, const uint8_t *B, uint8_t *tmp)
 {
-    int n = code->n;
-    for (int i = 0; i < n; i++)
-        if (!is_codeword(code, B + (size_t)i * n)) return 0;
-    for (int j = 0; j < n; j++) {
-        for (int i = 0; i < n; i++) tmp[i] = B[(size_t)i * n + j];
-        if (!is_codeword(code, tmp)) return 0;
+    int nr = row->n, nc = col->n;
+    for (int i = 0; i < nc; i++)
+        if (!is_codeword(row, B + (size_t)i * nr)) return 0;
+    for (int j = 0; j < nr; j++) {
+        for (int i = 0; i < nc; i++) tmp[i] = B[(size_t)i * nr + j];
+        if (!is_codeword(col, tmp)) return 0;
     }
     return 1;
 }
@@ -568,12 +569,12 @@ static int frame_valid(const oracle_code *code, const uint8_t *B, uint8_t *tmp)
  * status (0 decoded, 1 max iterations, 2 invalid input), total queries and
  * the "parallelized" count (sum over halves of the max per-word queries).
  */
-int oracle_product(const oracle_code *code, const float *lch, int L, int64_t cap, double thr, float alpha,
-                   int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
-                   int64_t *par_queries)
+int oracle_product2(const oracle_code *row, const oracle_code *col, const float *lch, int L, int64_t cap,
+                    double thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status,
+                    int64_t *queries, int64_t *par_queries)
 {
-    int n = code->n;
-    size_t nn = (size_t)n * n;
+    int nr = row->n, nc = col->n;
+    size_t nn = (size_t)nr * nc;
     float *LE = (float *)calloc(nn, sizeof(float));
     uint8_t *B = (uint8_t *)calloc(nn, 1);
     float wl[OR_NMAX], wa[OR_NMAX];
@@ -583,10 +584,14 @@ int oracle_product(const oracle_code *code, const float *lch, int L, int64_t cap
     int st = 1, h;
     for (h = 1; h <= 2 * max_iter; h++) {
         int rows = h & 1;
+        /* a row half decodes the n_col rows (row code, n_row bits each); a
+           column half the n_row columns (column code, n_col bits each) */
+        const oracle_code *code = rows ? row : col;
+        int nw = rows ? nc : nr, len = code->n;
         int64_t qmax = 0;
-        for (int w = 0; w < n; w++) {
-            for (int i = 0; i < n; i++) {
-                size_t pos = rows ? (size_t)w * n + i : (size_t)i * n + w;
+        for (int w = 0; w < nw; w++) {
+            for (int i = 0; i < len; i++) {
+                size_t pos = rows ? (size_t)w * nr + i : (size_t)i * nr + w;
                 wl[i] = lch[pos];
                 wa[i] = alpha * LE[pos]; /* FP32 product, no contraction */
             }
@@ -598,14 +603,14 @@ int oracle_product(const oracle_code *code, const float *lch, int L, int64_t cap
             }
             qsum += q;
             if (q > qmax) qmax = q;
-            for (int i = 0; i < n; i++) {
-                size_t pos = rows ? (size_t)w * n + i : (size_t)i * n + w;
+            for (int i = 0; i < len; i++) {
+                size_t pos = rows ? (size_t)w * nr + i : (size_t)i * nr + w;
                 LE[pos] = (float)lext[i];
                 B[pos] = hd[i];
             }
         }
         qpar += qmax;
-        if (frame_valid(code, B, tmp)) {
+        if (frame_valid(row, col, B, tmp)) {
             st = 0;
             break;
         }
@@ -620,4 +625,13 @@ done:
     free(LE);
     free(B);
     return 0;
+}
+
+/* square product code: the same code on rows and columns */
+int oracle_product(const oracle_code *code, const float *lch, int L, int64_t cap, double thr, float alpha,
+                   int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
+                   int64_t *par_queries)
+{
+    return oracle_product2(code, code, lch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
+                           par_queries);
 }

@@ -66,3 +66,30 @@ def test_bler_falls_with_snr(oracle_lib):
         err = (res["bits"] != X).reshape(300, -1).any(axis=1)
         bler.append(err.mean())
     assert bler[0] > 0.1 and bler[1] < 0.02
+
+
+def test_non_square_product_code(oracle_lib):
+    """Product of different row and column codes (an n_col x n_row frame):
+    rows are decoded with the row code, columns with the column code, and a
+    frame succeeds iff every row and every column is a codeword of its code."""
+    from workloads import awgn_frames, ebch
+    r, c = ebch("ebch_32_26"), ebch("ebch_16_11")
+    orc, occ = oracle_lib.OracleCode(r), oracle_lib.OracleCode(c)
+    U, X, L = awgn_frames(r, 24, 3.0, seed=41, col_code=c)
+    assert X.shape == (24, 16, 32)
+    res = oracle_lib.product_batch(orc, L, col=occ, L=4, cap=10**4, alpha=0.5, max_iter=10)
+    for f in range(24):
+        B = res["bits"][f]
+        ok = not r.syndrome(B).any() and not c.syndrome(B.T).any()
+        assert ok == (res["status"][f] == 0)
+    assert (res["status"] == 0).mean() > 0.8
+    # noiseless: one half suffices
+    clean = (8.0 * (1.0 - 2.0 * X[:2])).astype(np.float32)
+    res0 = oracle_lib.product_batch(orc, clean, col=occ, max_iter=4)
+    assert (res0["half_iters"] == 1).all() and (res0["bits"] == X[:2]).all()
+    # a square code through the two-code path equals the one-code path
+    Us, Xs, Ls = awgn_frames(c, 6, 2.5, seed=42)
+    a = oracle_lib.product_batch(occ, Ls, max_iter=6)
+    b = oracle_lib.product_batch(occ, Ls, max_iter=6, col=occ)
+    for k in ("bits", "half_iters", "status", "queries", "par_queries"):
+        np.testing.assert_array_equal(a[k], b[k])

@@ -156,6 +156,17 @@ class LinearCode:
         return np.ascontiguousarray(cols.reshape(F, self.n, self.n).transpose(0, 2, 1))
 
 
+def product_encode(row: LinearCode, col: LinearCode, U: np.ndarray) -> np.ndarray:
+    """[F, k_col, k_row] information blocks -> [F, n_col, n_row] product
+    codewords of the row and column codes (rows first, then columns): every
+    row is a row-code word, every column a column-code word."""
+    U = np.asarray(U, dtype=np.uint8)
+    F = U.shape[0]
+    rows = row.encode(U.reshape(F * col.k, row.k)).reshape(F, col.k, row.n)
+    cols = col.encode(np.ascontiguousarray(rows.transpose(0, 2, 1)).reshape(F * row.n, col.k))
+    return np.ascontiguousarray(cols.reshape(F, row.n, col.n).transpose(0, 2, 1))
+
+
 def ebch(name_or_nk) -> LinearCode:
     """Extended BCH code by name ('ebch_64_57') or by (n, k)."""
     if isinstance(name_or_nk, tuple):
