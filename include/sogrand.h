@@ -42,7 +42,7 @@ extern "C" {
 #define SOGRAND_ENOMEM 2       /* device or host allocation failed */
 #define SOGRAND_ECUDA 3        /* a CUDA runtime call failed */
 #define SOGRAND_ETIMEOUT 4     /* a bounded device wait gave up */
-#define SOGRAND_EUNSUPPORTED 5 /* valid but not implemented (e.g. row code != column code) */
+#define SOGRAND_EUNSUPPORTED 5 /* valid but not implemented (e.g. row and column codes of different kernel classes) */
 
 /* Opaque code object: parity-check matrix, its device copy and the query-order
  * tables.  Immutable after creation apart from table growth (see
@@ -132,17 +132,21 @@ int sogrand_decode_forney(sogrand_code *code, int64_t n_words, const float *llr_
  * halves) of every running frame with SOGRAND (lambda = L_Ch + fl32(alpha L_E)
  * of the previous half), takes the hard decision of L_APP and stops a frame
  * as soon as every row and column is a codeword; at most 2 * max_iter halves.
- *   row_code, col_code  the component codes (must be the same object;
- *                       EUNSUPPORTED otherwise)
- *   llr_ch     device [n_frames][n][n] channel LLRs, row-major (bit (i, j) is
- *              row i, column j)
- *   L, query_cap, thr   as for sogrand_decode (query_cap < 2^(n-1), so the
- *              search never exhausts the parity class)
+ *   row_code, col_code  the component codes: every row of a frame is a word
+ *              of the row code (n_row = its n), every column a word of the
+ *              column code (n_col = its n).  They may be the same object (a
+ *              square product code) or two codes of one kernel class: both n
+ *              in 1..32, in 33..64 or in 65..128, and both n - k <= 32 or both
+ *              above (EUNSUPPORTED otherwise).  Below, n x n reads n_col x n_row.
+ *   llr_ch     device [n_frames][n_col][n_row] channel LLRs, row-major (bit
+ *              (i, j) is row i, column j)
+ *   L, query_cap, thr   as for sogrand_decode (query_cap < 2^(n-1) for both
+ *              codes, so the search never exhausts a parity class)
  *   alpha      extrinsic scaling, > 0 (the paper uses 0.5)
  *   max_iter   1 <= max_iter <= 1000 full (row + column) iterations
  *   outputs (device):
- *   bits       [n_frames][ceil(n*n/8)] u8: the final hard decision, bit p =
- *              i*n + j at byte p/8, bit p%8 (required)
+ *   bits       [n_frames][ceil(n_col*n_row/8)] u8: the final hard decision,
+ *              bit p = i*n_row + j at byte p/8, bit p%8 (required)
  *   half_iters [n_frames] half iterations run (may be NULL)
  *   status     [n_frames] 0 decoded (all rows and columns codewords), 1 max
  *              iterations reached, 2 non-finite input (may be NULL)

@@ -211,18 +211,18 @@ def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: 
     batched form (product_decode_persistent), else one launch per half
     (product_decode_ex)."""
     import torch
-    F, n, n2 = llr_ch.shape
-    assert n == n2 == code.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
+    cc = col_code if col_code is not None else code
+    F, nc, nr = llr_ch.shape  # frames of n_col rows (column code's n) by n_row columns (row code's n)
+    assert nr == code.n and nc == cc.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
     dev = llr_ch.device
     if out is None:
-        out = dict(bits=torch.empty((F, (n * n + 7) // 8), dtype=torch.uint8, device=dev),
+        out = dict(bits=torch.empty((F, (nr * nc + 7) // 8), dtype=torch.uint8, device=dev),
                    half_iters=torch.empty(F, dtype=torch.int32, device=dev),
                    status=torch.empty(F, dtype=torch.uint8, device=dev),
                    queries=torch.empty(F, dtype=torch.int64, device=dev),
                    par_queries=torch.empty(F, dtype=torch.int64, device=dev),
                    weight_sum=torch.zeros(1, dtype=torch.int64, device=dev),
                    xf_words=torch.zeros(1, dtype=torch.int32, device=dev))
-    cc = col_code if col_code is not None else code
     st = None
     if stats:
         tm = (C.c_float * 2)()
@@ -277,11 +277,14 @@ def product_decode_mixed(groups, L: int = 4, query_cap: int = 10**4, thr: float 
 
 
 def product_decode_host(code: Code, llr_ch: np.ndarray, L: int = 4, query_cap: int = 10**4, thr: float = 0.0,
-                        alpha: float = 0.5, max_iter: int = 20, out=None, stream=None) -> dict:
+                        alpha: float = 0.5, max_iter: int = 20, out=None, stream=None,
+                        col_code: Code | None = None) -> dict:
     """product_decode on HOST buffers (numpy or pinned CPU torch tensors); copies inside the call."""
-    F, n, _ = llr_ch.shape
+    cc = col_code if col_code is not None else code
+    F, nc, nr = llr_ch.shape
+    assert nr == code.n and nc == cc.n
     if out is None:
-        out = dict(bits=np.empty((F, (n * n + 7) // 8), np.uint8), half_iters=np.empty(F, np.int32),
+        out = dict(bits=np.empty((F, (nr * nc + 7) // 8), np.uint8), half_iters=np.empty(F, np.int32),
                    status=np.empty(F, np.uint8), queries=np.empty(F, np.int64))
 
     def hp(a):
@@ -289,7 +292,7 @@ def product_decode_host(code: Code, llr_ch: np.ndarray, L: int = 4, query_cap: i
             return None
         return C.c_void_p(a.data_ptr()) if hasattr(a, "data_ptr") else a.ctypes.data_as(C.c_void_p)
 
-    rc = load().product_decode_host(code.handle, code.handle, F, hp(llr_ch), int(L), int(query_cap), float(thr),
+    rc = load().product_decode_host(code.handle, cc.handle, F, hp(llr_ch), int(L), int(query_cap), float(thr),
                                     float(alpha), int(max_iter), hp(out["bits"]), hp(out["half_iters"]),
                                     hp(out["status"]), hp(out["queries"]), _stream(stream))
     _check(rc, "product_decode_host")
@@ -372,11 +375,12 @@ def sogrand_int_peak(trips: int = 150_000, stream=None):
     return ops.value, ms.value
 
 
-def unpack_bits(bits, n: int):
-    """[F, ceil(n*n/8)] u8 (LSB first) -> [F, n, n] u8 (numpy)."""
+def unpack_bits(bits, n: int, n_row: int | None = None):
+    """[F, ceil(n*n_row/8)] u8 (LSB first) -> [F, n, n_row] u8 (numpy); n_row defaults to n."""
+    nr = n if n_row is None else n_row
     b = np.asarray(bits.cpu() if hasattr(bits, "cpu") else bits, dtype=np.uint8)
     F = b.shape[0]
-    return np.unpackbits(b, axis=1, bitorder="little")[:, :n * n].reshape(F, n, n)
+    return np.unpackbits(b, axis=1, bitorder="little")[:, :n * nr].reshape(F, n, nr)
 
 
 def unpack_words(words, n: int):

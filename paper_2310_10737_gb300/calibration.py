@@ -67,6 +67,27 @@ def list_bler_calibration(code: Code, llr, X, L: int = 4, query_cap: int = 10**4
                         "forney": (float(pred_f.sum()), int(miss_f.sum()))}}
 
 
+def bit_probability_bins(code: Code, llr, X, L: int = 4, query_cap: int = 10**4, nbins: int = 20) -> list:
+    """The paper's form of the bitwise check (Fig. BER_prediction): the
+    predicted probability that a bit is 1, 1 / (1 + e^L_APP), in equal-width
+    bins, against the frequency of 1 among the transmitted bits of each bin."""
+    out = sogrand_decode(code, llr, L=L, query_cap=query_cap, lists=False)
+    lapp = out["llr_app"].cpu().numpy().astype(np.float64)
+    with np.errstate(over="ignore"):
+        p1 = 1.0 / (1.0 + np.exp(lapp))
+    ones = np.asarray(X, dtype=np.uint8) == 1
+    edges = np.linspace(0.0, 1.0, nbins + 1)
+    edges[-1] = 1.0 + 1e-12
+    rows = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (p1 >= lo) & (p1 < hi)
+        cnt = int(sel.sum())
+        rows.append({"lo": float(lo), "hi": float(min(hi, 1.0)), "count": cnt,
+                     "predicted": float(p1[sel].mean()) if cnt else None,
+                     "empirical": float(ones[sel].mean()) if cnt else None})
+    return rows
+
+
 def bit_calibration(code: Code, llr, X, L: int = 4, query_cap: int = 10**4, forney: bool = False, edges=None,
                     min_count: int = 2000) -> list:
     """Binned predicted bit-error probability 1/(1+e^|L_APP|) vs the observed

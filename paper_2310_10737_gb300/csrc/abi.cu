@@ -338,6 +338,16 @@ cudaError_t scratch_alloc(char **p, size_t bytes, cudaStream_t s) {
   return cudaMallocFromPoolAsync((void **)p, bytes, pool, s);
 }
 
+// Row and column codes of a product code: the same code, or two codes of the
+// same kernel class (bits per lane and syndrome width), which one
+// instantiation of the product kernels decodes.
+int pair_check(const sogrand_code *r, const sogrand_code *c) {
+  if (r == c) return SOGRAND_OK;
+  auto npl = [](int n) { return n <= 32 ? 1 : (n <= 64 ? 2 : 4); };
+  if (npl(r->n) != npl(c->n) || (r->m > 32) != (c->m > 32) || r->device != c->device) return SOGRAND_EUNSUPPORTED;
+  return SOGRAND_OK;
+}
+
 int ensure_cap(sogrand_code *c, int64_t cap) {
   std::lock_guard<std::mutex> g(c->mu);
   int dev = 0;
@@ -359,7 +369,7 @@ cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P
                                   cudaStream_t s) {
   const sg::DevCode d = dev_code(c);
   cudaError_t e = cudaSuccess;
-  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, P, a, s)));
+  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, d, P, a, s)));
   return e;
 }
 int sm_count_of_device() {
@@ -520,18 +530,21 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   if (!rc_ || !cc_ || F < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f) ||
       !(alpha > 0.f && alpha < 1e6f) || max_iter < 1 || max_iter > 1000)
     return SOGRAND_EINVAL;
-  if (rc_ != cc_) return SOGRAND_EUNSUPPORTED;
-  sogrand_code *c = rc_;
-  if (c->n - 1 < 63 && cap >= (int64_t(1) << (c->n - 1))) return SOGRAND_EINVAL;
+  int rc = pair_check(rc_, cc_);
+  if (rc != SOGRAND_OK) return rc;
+  sogrand_code *c = rc_, *cc = const_cast<sogrand_code *>(cc_);
+  for (const sogrand_code *x : {(const sogrand_code *)c, cc_})
+    if (x->n - 1 < 63 && cap >= (int64_t(1) << (x->n - 1))) return SOGRAND_EINVAL;
   if (F == 0) return SOGRAND_OK;
   if (!llr_ch || !bits) return SOGRAND_EINVAL;
-  int rc = ensure_cap(c, cap);
+  rc = ensure_cap(c, cap);
+  if (rc == SOGRAND_OK && cc != c) rc = ensure_cap(cc, cap);
   if (rc != SOGRAND_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = c->n, nm = c->nm;
+  const int nr = c->n, nc = cc->n, nm = c->nm, hbw = std::max(nr, nc);
   // scratch, stream-ordered
-  const size_t b_le = (size_t)F * n * n * sizeof(float);
-  const size_t b_hb = (size_t)F * n * nm * sizeof(uint64_t);
+  const size_t b_le = (size_t)F * nr * nc * sizeof(float);
+  const size_t b_hb = (size_t)F * hbw * nm * sizeof(uint64_t);
   const size_t b_i32 = (size_t)F * sizeof(int32_t);
   const size_t b_i64 = (size_t)F * sizeof(int64_t);
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
@@ -548,6 +561,9 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   };
   sg::ProductArgs a{};
   a.n_frames = F;
+  a.nr = nr;
+  a.nc = nc;
+  a.hbw = hbw;
   a.llr_ch = llr_ch;
   a.alpha = alpha;
   a.max_half = 2 * max_iter;
@@ -563,7 +579,7 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   a.active = (int32_t *)take(sizeof(int32_t));
   a.xf_count = stats ? stats->xf_words : nullptr;
   a.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
-  sg::DevCode d = dev_code(c);
+  sg::DevCode d = dev_code(c), dcol = dev_code(cc);
   sg::SisoParams P{L, (int32_t)cap, thr};
   cudaError_t e = cudaSuccess;
   const bool timed = stats && stats->timing_ms;
@@ -575,12 +591,12 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_init<NPL, SYN>(d, a, s)));
   for (int h = 1; h <= a.max_half && e == cudaSuccess; h++) {
     if (timed) e = cudaEventRecord(ev[0], s);
-    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, P, a, h, s)));
+    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, dcol, P, a, h, s)));
     if (e != cudaSuccess) break;
     launches++;
     if (timed) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.active, 0, sizeof(int32_t), s);
-    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, a, h, s)));
+    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, dcol, a, h, s)));
     if (e != cudaSuccess) break;
     launches++;
     if (timed) e = cudaEventRecord(ev[2], s);
@@ -618,10 +634,13 @@ int persistent_check(const sogrand_code *rc_, const sogrand_code *cc_, int64_t F
   if (!rc_ || !cc_ || F < 0 || L < 1 || L > sg::LMAX || cap < 1 || cap > MAX_CAP || !(thr >= 0.f && thr < 1.f) ||
       !(alpha > 0.f && alpha < 1e6f) || max_iter < 1 || max_iter > 1000)
     return SOGRAND_EINVAL;
-  if (rc_ != cc_) return SOGRAND_EUNSUPPORTED;
-  if (rc_->n - 1 < 63 && cap >= (int64_t(1) << (rc_->n - 1))) return SOGRAND_EINVAL;
-  // word tickets (slots x n, plus one per idle warp) are 32-bit
-  if (F * 2 * (int64_t)max_iter * rc_->n >= (int64_t(1) << 31) - (int64_t(1) << 22)) return SOGRAND_EINVAL;
+  const int prc = pair_check(rc_, cc_);
+  if (prc != SOGRAND_OK) return prc;
+  for (const sogrand_code *x : {rc_, cc_})
+    if (x->n - 1 < 63 && cap >= (int64_t(1) << (x->n - 1))) return SOGRAND_EINVAL;
+  // word tickets (slots x the larger n, plus one per idle warp) are 32-bit
+  if (F * 2 * (int64_t)max_iter * std::max(rc_->n, cc_->n) >= (int64_t(1) << 31) - (int64_t(1) << 22))
+    return SOGRAND_EINVAL;
   return SOGRAND_OK;
 }
 
@@ -630,9 +649,10 @@ inline size_t al256(size_t x) { return (x + 255) & ~size_t(255); }
 // Scratch of one batched decode of F frames: L_E state, hard decisions, the
 // per-frame counters, the frame-half list, room for every optional output and
 // the control words.  Every sub-buffer starts on a 256-byte boundary.
-size_t persistent_scratch_bytes(int64_t F, int n, int nm, int max_iter) {
+size_t persistent_scratch_bytes(int64_t F, int nr, int nc, int nm, int max_iter) {
   const size_t b_i32 = (size_t)F * sizeof(int32_t), b_i64 = (size_t)F * sizeof(int64_t);
-  return al256((size_t)F * n * n * sizeof(float)) + al256((size_t)F * n * nm * sizeof(uint64_t)) + 5 * al256(b_i32) +
+  return al256((size_t)F * nr * nc * sizeof(float)) + al256((size_t)F * std::max(nr, nc) * nm * sizeof(uint64_t)) +
+         5 * al256(b_i32) +
          al256((size_t)F * 2 * max_iter * sizeof(int32_t)) + 2 * al256(b_i64) + al256((size_t)F) +
          al256(4 * sizeof(int32_t));
 }
@@ -640,11 +660,11 @@ size_t persistent_scratch_bytes(int64_t F, int n, int nm, int max_iter) {
 // Queue set-up and the persistent kernel for F frames on stream s (nothing
 // is waited for).  Outputs that are null go to the scratch.  *err_dev is the
 // device word that holds the kernel's timeout flag afterwards.
-cudaError_t persistent_enqueue(sogrand_code *c, int64_t F, const float *llr_ch, const sg::SisoParams &P, float alpha,
-                               int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
-                               int64_t *par_queries, unsigned long long *wsum, int32_t *xf, char *mem,
-                               cudaStream_t s, int32_t **err_dev) {
-  const int n = c->n, nm = c->nm;
+cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t F, const float *llr_ch,
+                               const sg::SisoParams &P, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                               uint8_t *status, int64_t *queries, int64_t *par_queries, unsigned long long *wsum,
+                               int32_t *xf, char *mem, cudaStream_t s, int32_t **err_dev) {
+  const int nr = c->n, nc = cc->n, nm = c->nm, hbw = std::max(nr, nc);
   char *p = mem;
   auto take = [&p](size_t bytes) {
     char *r = p;
@@ -654,11 +674,14 @@ cudaError_t persistent_enqueue(sogrand_code *c, int64_t F, const float *llr_ch, 
   const size_t b_i32 = (size_t)F * sizeof(int32_t), b_i64 = (size_t)F * sizeof(int64_t);
   sg::ProductArgs a{};
   a.n_frames = F;
+  a.nr = nr;
+  a.nc = nc;
+  a.hbw = hbw;
   a.llr_ch = llr_ch;
   a.alpha = alpha;
   a.max_half = 2 * max_iter;
-  a.le = (float *)take((size_t)F * n * n * sizeof(float));
-  a.hb = (uint64_t *)take((size_t)F * n * nm * sizeof(uint64_t));
+  a.le = (float *)take((size_t)F * nr * nc * sizeof(float));
+  a.hb = (uint64_t *)take((size_t)F * hbw * nm * sizeof(uint64_t));
   a.hmax = (int32_t *)take(b_i32);
   a.half_cur = (int32_t *)take(b_i32);
   a.done_words = (int32_t *)take(b_i32);
@@ -678,9 +701,9 @@ cudaError_t persistent_enqueue(sogrand_code *c, int64_t F, const float *llr_ch, 
   a.xf_count = xf;
   a.wsum = wsum;
   *err_dev = a.ctrl + 3;
-  sg::DevCode d = dev_code(c);
+  sg::DevCode d = dev_code(c), dcol = dev_code(cc);
   cudaError_t e = cudaSuccess;
-  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, P, a, s)));
+  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, dcol, P, a, s)));
   return e;
 }
 
@@ -697,12 +720,13 @@ int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_
   if (rc != SOGRAND_OK) return rc;
   if (F == 0) return SOGRAND_OK;
   if (!llr_ch || !bits) return SOGRAND_EINVAL;
-  sogrand_code *c = rc_;
+  sogrand_code *c = rc_, *cc = const_cast<sogrand_code *>(cc_);
   rc = ensure_cap(c, cap);
+  if (rc == SOGRAND_OK && cc != c) rc = ensure_cap(cc, cap);
   if (rc != SOGRAND_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   char *mem = nullptr;
-  if (scratch_alloc(&mem, persistent_scratch_bytes(F, c->n, c->nm, max_iter), s) != cudaSuccess)
+  if (scratch_alloc(&mem, persistent_scratch_bytes(F, c->n, cc->n, c->nm, max_iter), s) != cudaSuccess)
     return SOGRAND_ENOMEM;
   const sg::SisoParams P{L, (int32_t)cap, thr};
   const bool timed = stats && stats->timing_ms;
@@ -713,7 +737,7 @@ int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_
   if (e == cudaSuccess && timed) e = cudaEventRecord(ev[0], s);
   int32_t *err_dev = nullptr;
   if (e == cudaSuccess)
-    e = persistent_enqueue(c, F, llr_ch, P, alpha, max_iter, bits, half_iters, status, queries,
+    e = persistent_enqueue(c, cc, F, llr_ch, P, alpha, max_iter, bits, half_iters, status, queries,
                            stats ? stats->par_queries : nullptr,
                            stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr,
                            stats ? stats->xf_words : nullptr, mem, s, &err_dev);
@@ -789,12 +813,13 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   if (rc != SOGRAND_OK) return rc;
   if (F == 0) return SOGRAND_OK;
   if (!llr_ch || !bits) return SOGRAND_EINVAL;
-  sogrand_code *c = rc_;
+  sogrand_code *c = rc_, *cc = const_cast<sogrand_code *>(cc_);
   rc = ensure_cap(c, cap);
+  if (rc == SOGRAND_OK && cc != c) rc = ensure_cap(cc, cap);
   if (rc != SOGRAND_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
-  const int n = c->n, nm = c->nm;
-  const size_t in_f = (size_t)n * n * sizeof(float), nb = ((size_t)n * n + 7) / 8;
+  const int nr = c->n, nc = cc->n, nm = c->nm;
+  const size_t in_f = (size_t)nr * nc * sizeof(float), nb = ((size_t)nr * nc + 7) / 8;
   // Chunks of the batch move through three stages on their own streams:
   // copy in (h2d), decode (two streams taking chunks in turn, so the tail of
   // one chunk overlaps the start of the next), copy out (d2h).  Events order
@@ -803,7 +828,7 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   const int64_t chunk = (F + K - 1) / K;
   const size_t b_in = al256((size_t)F * in_f), b_bits = al256((size_t)F * nb);
   const size_t b_out = b_in + b_bits + al256((size_t)F * 4) + al256((size_t)F) + al256((size_t)F * 8);
-  const size_t b_scr = al256(persistent_scratch_bytes(chunk, n, nm, max_iter));
+  const size_t b_scr = al256(persistent_scratch_bytes(chunk, nr, nc, nm, max_iter));
   char *mem = nullptr;
   if (scratch_alloc(&mem, b_out + 2 * b_scr + 256, s) != cudaSuccess) return SOGRAND_ENOMEM;
   float *d_in = (float *)mem;
@@ -839,7 +864,7 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
     if (e == cudaSuccess) e = cudaStreamWaitEvent(sd, in_done, 0);
     int32_t *err_k = nullptr;
     if (e == cudaSuccess)
-      e = persistent_enqueue(c, Fk, (const float *)((const char *)d_in + f0 * in_f), P, alpha, max_iter,
+      e = persistent_enqueue(c, cc, Fk, (const float *)((const char *)d_in + f0 * in_f), P, alpha, max_iter,
                              d_bits + f0 * nb, d_hi + f0, d_st + f0, d_q + f0, nullptr, nullptr, nullptr,
                              mem + b_out + (k & 1) * b_scr, sd, &err_k);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_err + k, err_k, sizeof(int32_t), cudaMemcpyDeviceToDevice, sd);
@@ -904,7 +929,8 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   size_t bytes = 0;
   for (int g = 0; g < n_groups; g++) {
     off[g] = bytes;
-    bytes += al256(persistent_scratch_bytes(groups[g].n_frames, groups[g].code->n, groups[g].code->nm, max_iter));
+    bytes += al256(persistent_scratch_bytes(groups[g].n_frames, groups[g].code->n, groups[g].code->n,
+                                            groups[g].code->nm, max_iter));
   }
   const size_t o_queue = bytes, o_ctrl = o_queue + al256((size_t)total * max_half * sizeof(int32_t));
   const size_t o_tab = o_ctrl + 256, total_bytes = o_tab + al256(n_groups * sizeof(sg::MixGroup));
@@ -948,6 +974,7 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
     a.queries = G.queries ? G.queries : q_s;
     a.par_queries = pq_s;
     a.status = G.status ? G.status : st_s;
+    a.nr = a.nc = a.hbw = c->n;
     a.ctrl = (int32_t *)(mem + o_ctrl);  // a lock timeout in a word stops the launch
     sg::MixGroup &M = tab[g];
     M.code = dev_code(c);
@@ -1106,6 +1133,7 @@ int product_decode_noalloc(sogrand_code *rc_, const sogrand_code *cc_, int64_t F
   cudaStream_t s = (cudaStream_t)stream;
   sg::ProductArgs a{};
   a.n_frames = F;
+  a.nr = a.nc = a.hbw = c->n;
   a.llr_ch = llr_ch;
   a.alpha = alpha;
   a.max_half = 2 * max_iter;
@@ -1128,8 +1156,8 @@ int product_decode_noalloc(sogrand_code *rc_, const sogrand_code *cc_, int64_t F
   // every half iteration is launched; the kernels skip frames that finished,
   // so the host never waits on the device
   for (int h = 1; h <= a.max_half && e == cudaSuccess; h++) {
-    SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, P, a, h, s)));
-    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, a, h, s)));
+    SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, d, P, a, h, s)));
+    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, d, a, h, s)));
   }
   return e == cudaSuccess ? SOGRAND_OK : SOGRAND_ECUDA;
 }

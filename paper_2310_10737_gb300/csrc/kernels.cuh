@@ -151,6 +151,8 @@ struct WarpTally {
 // One component word of frame f in half `half` (rows when odd): lambda =
 // L_Ch + fl32(alpha L_E) (L_A = 0 in the first half), SOGRAND, then L_E and
 // the hard decision of L_APP are stored and the query counters updated.
+// `code` is the code of this half's words (the row code in a row half, the
+// column code in a column half); the frame is a.nc rows of a.nr bits.
 // Returns the word's query count (-1: non-finite input).
 template <int NPL, class SYN, bool COHERENT>
 __device__ __forceinline__ int product_word(const DevCode &code, const SisoParams &P, const ProductArgs &a,
@@ -160,16 +162,16 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
 #ifdef SG_PHASE_PROFILE
   const long long t0 = clock64();
 #endif
-  const int n = code.n;
+  const int n = code.n, nr = a.nr;
   const bool rows = (half & 1) != 0;
-  const size_t fb = (size_t)f * n * n;
+  const size_t fb = (size_t)f * nr * a.nc;
   float lam[NPL];
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
     const int i = lane + 32 * k;
     float x = 0.f;
     if (i < n) {
-      const size_t pos = fb + (rows ? (size_t)wd * n + i : (size_t)i * n + wd);
+      const size_t pos = fb + (rows ? (size_t)wd * nr + i : (size_t)i * nr + wd);
       x = __ldg(a.llr_ch + pos);
       if (half > 1) x = __fadd_rn(x, __fmul_rn(a.alpha, ld_state<COHERENT>(a.le + pos)));  // L_A = alpha L_E
     }
@@ -185,13 +187,13 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
   for (int k = 0; k < NPL; k++) {
     const int i = lane + 32 * k;
     if (i < n) {
-      const size_t pos = fb + (rows ? (size_t)wd * n + i : (size_t)i * n + wd);
+      const size_t pos = fb + (rows ? (size_t)wd * nr + i : (size_t)i * nr + wd);
       a.le[pos] = (empty || res.queries < 0) ? 0.f : __fsub_rn(lapp[k], lam[k]);
     }
     hb[k] = __ballot_sync(FULL, i < n && lapp[k] < 0.f);
   }
   if (lane == 0) {
-    uint64_t *dst = a.hb + ((size_t)f * n + wd) * NM;
+    uint64_t *dst = a.hb + ((size_t)f * a.hbw + wd) * NM;
 #pragma unroll
     for (int wd2 = 0; wd2 < NM; wd2++) {
       uint64_t v = hb[2 * wd2];
@@ -216,37 +218,38 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
   return res.queries;
 }
 
-// Hard decision of frame f after a half: W holds its n words (rows after an
-// odd half, columns after an even one).  Every word of this orientation is a
-// codeword iff parity(word & H row t) = 0 for all t; every word of the other
-// orientation is a codeword iff, for every t, the XOR of the words selected
-// by H row t is zero (bit-sliced, no transpose).  Warp-uniform result.
+// Hard decision of frame f after a half: W holds its words (rows after an
+// odd half, columns after an even one): xc.n words of wc.n bits, wc the code
+// of these words and xc the code across them.  Every word is a codeword of wc
+// iff parity(word & H_wc row t) = 0 for all t; every word of the other
+// orientation is a codeword of xc iff, for every t, the XOR of the words
+// selected by H_xc row t is zero (bit-sliced, no transpose).  Warp-uniform.
 template <int NPL>
-__device__ __forceinline__ bool frame_valid(const DevCode &code, const uint64_t *W, int lane) {
+__device__ __forceinline__ bool frame_valid(const DevCode &wc, const DevCode &xc, const uint64_t *W, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
-  const int n = code.n, m = code.m;
+  const int nw = xc.n;  // words in W
   bool ok = true;
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
     const int wd = lane + 32 * k;
-    if (wd < n) {
-      for (int t = 0; t < m && ok; t++) {
+    if (wd < nw) {
+      for (int t = 0; t < wc.m && ok; t++) {
         int p = 0;
 #pragma unroll
-        for (int x = 0; x < NM; x++) p ^= __popcll(W[wd * NM + x] & __ldg(code.hrow + t * NM + x));
+        for (int x = 0; x < NM; x++) p ^= __popcll(W[wd * NM + x] & __ldg(wc.hrow + t * NM + x));
         if (p & 1) ok = false;
       }
     }
   }
   ok = __all_sync(FULL, ok);
-  for (int t = 0; t < m && ok; t++) {
+  for (int t = 0; t < xc.m && ok; t++) {
     uint64_t acc[NM];
 #pragma unroll
     for (int x = 0; x < NM; x++) acc[x] = 0;
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
       const int wd = lane + 32 * k;
-      if (wd < n && ((__ldg(code.hrow + t * NM + (wd >> 6)) >> (wd & 63)) & 1ull))
+      if (wd < nw && ((__ldg(xc.hrow + t * NM + (wd >> 6)) >> (wd & 63)) & 1ull))
 #pragma unroll
         for (int x = 0; x < NM; x++) acc[x] ^= W[wd * NM + x];
     }
@@ -266,19 +269,19 @@ __device__ __forceinline__ bool frame_valid(const DevCode &code, const uint64_t 
 // words of the last half: rows (bit j of word i is bit (i, j)) or columns
 // (bit i of word j is bit (i, j)).
 template <int NPL>
-__device__ __forceinline__ void frame_finish(const DevCode &code, const ProductArgs &a, int64_t f, bool rows,
-                                             int half, int status, const uint64_t *W, int lane) {
+__device__ __forceinline__ void frame_finish(const ProductArgs &a, int64_t f, bool rows, int half, int status,
+                                             const uint64_t *W, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
-  const int n = code.n;
-  const int nbytes = (n * n + 7) / 8;
+  const int nr = a.nr, nbits = a.nr * a.nc;
+  const int nbytes = (nbits + 7) / 8;
   uint8_t *out = a.bits + (size_t)f * nbytes;
   for (int by = lane; by < nbytes; by += 32) {
     unsigned v = 0;
 #pragma unroll
     for (int t = 0; t < 8; t++) {
       const int p = by * 8 + t;
-      if (p < n * n) {
-        const int i = p / n, j = p - i * n;
+      if (p < nbits) {
+        const int i = p / nr, j = p - i * nr;
         const uint64_t word = rows ? W[i * NM + (j >> 6)] >> (j & 63) : W[j * NM + (i >> 6)] >> (i & 63);
         v |= (unsigned)(word & 1ull) << t;
       }
@@ -294,15 +297,17 @@ __device__ __forceinline__ void frame_finish(const DevCode &code, const ProductA
 
 // ---- plain form: one launch per half iteration, then a check launch ----
 template <int NPL, class SYN, bool ROWS, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode code, const SisoParams P, const ProductArgs a,
-                                                      int half) {
+__global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode rowc, const DevCode colc, const SisoParams P,
+                                                         const ProductArgs a, int half) {
   extern __shared__ __align__(16) unsigned char smem[];
   using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
+  const int jm = max(rowc.jmax, colc.jmax);
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(jm));
   Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(code.jmax));
-  const int n = code.n;
+  bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(jm));
+  const DevCode &code = ROWS ? rowc : colc;  // the code of this half's words
+  const int n = ROWS ? a.nc : a.nr;          // words per frame in this half
   const int64_t items = a.n_frames * n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   WarpTally tally;
@@ -320,21 +325,23 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode code, 
 
 // One warp per frame.
 template <int NPL, class SYN>
-__global__ void __launch_bounds__(TPB) k_product_check(const DevCode code, const ProductArgs a, int half) {
+__global__ void __launch_bounds__(TPB) k_product_check(const DevCode rowc, const DevCode colc, const ProductArgs a,
+                                                       int half) {
   constexpr int NM = (32 * NPL + 63) / 64;
   constexpr int NT = 32 * NPL;
   __shared__ uint64_t words_s[WARPS_PER_BLOCK][NT * NM];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int n = code.n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   const bool rows = (half & 1) != 0;
+  const DevCode &wc = rows ? rowc : colc, &xc = rows ? colc : rowc;
+  const int n = xc.n;  // words of the last half
   for (int64_t f = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp; f < a.n_frames; f += nwarps) {
     const int32_t st = a.fstate[f];
     if (st != F_RUN && st != F_BAD_PENDING) continue;
     uint64_t *W = words_s[warp];
-    for (int x = lane; x < n * NM; x += 32) W[x] = a.hb[(size_t)f * n * NM + x];
+    for (int x = lane; x < n * NM; x += 32) W[x] = a.hb[(size_t)f * a.hbw * NM + x];
     __syncwarp();
-    const bool ok = frame_valid<NPL>(code, W, lane);
+    const bool ok = frame_valid<NPL>(wc, xc, W, lane);
     const bool bad = st == F_BAD_PENDING;
     const bool finish = bad || ok || half >= a.max_half;
     if (lane == 0) {
@@ -346,7 +353,7 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode code, const
       __syncwarp();
       continue;
     }
-    frame_finish<NPL>(code, a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, lane);
+    frame_finish<NPL>(a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, lane);
     if (lane == 0) a.fstate[f] = bad ? F_BAD : (ok ? F_DECODED : F_MAXIT);
     __syncwarp();
   }
@@ -406,16 +413,16 @@ __device__ __forceinline__ int sched_take(int32_t *ctrl_w, const volatile int32_
 // index space `gf`): check the frame and finish it, park it (a serving epoch
 // ran out: its state stays for the next launch) or append its next half.
 template <int NPL>
-__device__ __forceinline__ void frame_after_half(const DevCode &code, const ProductArgs &a, int32_t *ctrl,
-                                                 int32_t *queue_w, int64_t f, int64_t gf, int half, uint64_t *W,
-                                                 int lane) {
+__device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCode &xc, const ProductArgs &a,
+                                                 int32_t *ctrl, int32_t *queue_w, int64_t f, int64_t gf, int half,
+                                                 uint64_t *W, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
-  const int n = code.n;
+  const int n = xc.n;  // words of this half
   __threadfence();
   const bool rows = (half & 1) != 0;
-  for (int x = lane; x < n * NM; x += 32) W[x] = ld_state<true>(a.hb + (size_t)f * n * NM + x);
+  for (int x = lane; x < n * NM; x += 32) W[x] = ld_state<true>(a.hb + (size_t)f * a.hbw * NM + x);
   __syncwarp();
-  const bool ok = frame_valid<NPL>(code, W, lane);
+  const bool ok = frame_valid<NPL>(wc, xc, W, lane);
   int bad = 0, stop = 0;
   if (lane == 0) {
     bad = __ldcg(a.bad + f);
@@ -426,7 +433,7 @@ __device__ __forceinline__ void frame_after_half(const DevCode &code, const Prod
   bad = __shfl_sync(FULL, bad, 0);
   stop = __shfl_sync(FULL, stop, 0);
   if (bad || ok || half >= a.max_half) {
-    frame_finish<NPL>(code, a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, lane);
+    frame_finish<NPL>(a, f, rows, half, bad ? 2 : (ok ? 0 : 1), W, lane);
     __threadfence();
     if (lane == 0) atomicAdd(ctrl + 2, 1);
   } else if (half >= stop) {
@@ -455,25 +462,30 @@ __device__ __forceinline__ void frame_after_half(const DevCode &code, const Prod
 // bounded (a.max_spin microseconds of accumulated sleep without progress):
 // the kernel then records an error and every warp returns.
 template <int NPL, class SYN, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode code, const SisoParams P,
-                                                               const ProductArgs a) {
+__global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode rowc, const DevCode colc,
+                                                               const SisoParams P, const ProductArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
+  const int jm = max(rowc.jmax, colc.jmax);
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(jm));
   Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(code.jmax));
-  const int n = code.n;
+  bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(jm));
+  const int slot_n = max(a.nr, a.nc);  // tickets per list slot: the larger number of words in a half
   const int64_t nslots = a.n_frames * (int64_t)a.max_half;  // a frame has at most max_half halves
   WarpTally tally;
   for (;;) {
     int slot, w, f1;
-    if (!sched_take(a.ctrl, a.queue, nslots, a.n_frames, n, a.max_spin, lane, &slot, &w, &f1)) break;
+    if (!sched_take(a.ctrl, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1)) break;
     const int64_t li = (int64_t)f1 - 1;  // list index
     const int64_t f = a.frame_list ? (int64_t)a.frame_list[li] : li;
     int half = 0;
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
+    const bool rows = (half & 1) != 0;
+    const DevCode &code = rows ? rowc : colc, &xcode = rows ? colc : rowc;
+    const int n = xcode.n;  // words in this half
+    if (w >= n) continue;   // a ticket past this half's words (codes of different lengths)
     const int q = product_word<NPL, SYN, true>(code, P, a, sc, f, w, half, lane, tally);
     if (lane == 0 && q < 0) atomicExch(a.bad + f, 1);
     __threadfence();  // release this word's L_E and hard decision
@@ -482,7 +494,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
     if (lane == 0) done = atomicAdd(a.done_words + f, 1);
     done = __shfl_sync(FULL, done, 0);
     if (done != n - 1) continue;
-    frame_after_half<NPL>(code, a, a.ctrl, a.queue, f, li, half, sc.W(), lane);
+    frame_after_half<NPL>(code, xcode, a, a.ctrl, a.queue, f, li, half, sc.W(), lane);
   }
   tally.flush(a, lane);
 }
@@ -553,13 +565,13 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
     if (done != G.code.n - 1) continue;
     // the check uses this warp's word area as laid out for the group's NPL
     if (npl == 1)
-      frame_after_half<1>(G.code, G.a, m.ctrl, m.queue, f, gf, half,
+      frame_after_half<1>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
                           reinterpret_cast<uint64_t *>(wsm + Layout<1, SYN>::o_w), lane);
     else if (npl == 2)
-      frame_after_half<2>(G.code, G.a, m.ctrl, m.queue, f, gf, half,
+      frame_after_half<2>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
                           reinterpret_cast<uint64_t *>(wsm + Layout<2, SYN>::o_w), lane);
     else
-      frame_after_half<4>(G.code, G.a, m.ctrl, m.queue, f, gf, half,
+      frame_after_half<4>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
                           reinterpret_cast<uint64_t *>(wsm + Layout<4, SYN>::o_w), lane);
   }
   if (lane == 0) {
@@ -693,28 +705,30 @@ cudaError_t launch_trace(const DevCode &code, const float *lam, int max_q, uint6
 }
 
 template <int NPL, class SYN>
-cudaError_t launch_product_half(const DevCode &code, const SisoParams &P, const ProductArgs &a, int half,
-                                cudaStream_t s) {
-  const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
-  const int64_t items = a.n_frames * code.n;
+cudaError_t launch_product_half(const DevCode &rowc, const DevCode &colc, const SisoParams &P, const ProductArgs &a,
+                                int half, cudaStream_t s) {
+  const int smem = block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
+  const int64_t items = a.n_frames * ((half & 1) ? a.nc : a.nr);
+  const int minb = rowc.minb;
   if (half & 1) {
-    auto kern = code.minb == 8 ? k_product_half<NPL, SYN, true, 8> : k_product_half<NPL, SYN, true, 6>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, true, 8> : k_product_half<NPL, SYN, true, 6>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(code, P, a, half);
+    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
   } else {
-    auto kern = code.minb == 8 ? k_product_half<NPL, SYN, false, 8> : k_product_half<NPL, SYN, false, 6>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, false, 8> : k_product_half<NPL, SYN, false, 6>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
-    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(code, P, a, half);
+    kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
   }
   return cudaGetLastError();
 }
 
 template <int NPL, class SYN>
-cudaError_t launch_product_check(const DevCode &code, const ProductArgs &a, int half, cudaStream_t s) {
+cudaError_t launch_product_check(const DevCode &rowc, const DevCode &colc, const ProductArgs &a, int half,
+                                 cudaStream_t s) {
   auto kern = k_product_check<NPL, SYN>;
-  kern<<<grid_for(kern, 0, a.n_frames), TPB, 0, s>>>(code, a, half);
+  kern<<<grid_for(kern, 0, a.n_frames), TPB, 0, s>>>(rowc, colc, a, half);
   return cudaGetLastError();
 }
 
@@ -729,24 +743,25 @@ cudaError_t launch_product_init(const DevCode &code, const ProductArgs &a, cudaS
 }
 
 template <int NPL, class SYN>
-cudaError_t launch_product_persistent(const DevCode &code, const SisoParams &P, const ProductArgs &a, cudaStream_t s) {
+cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, const SisoParams &P,
+                                      const ProductArgs &a, cudaStream_t s) {
   if (a.n_frames <= 0) return cudaSuccess;
   k_persistent_init<<<(int)std::min<int64_t>((a.n_frames + 255) / 256, 4096), 256, 0, s>>>(a);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
-  auto kern = code.minb == 8 ? k_product_persistent<NPL, SYN, 8> : k_product_persistent<NPL, SYN, 6>;
+  const int smem = block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
+  auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8> : k_product_persistent<NPL, SYN, 6>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TPB, smem);
   if (occ < 1) occ = 1;
   // every block resident at once, no more warps than words of the batch
-  const int64_t want = (a.n_frames * code.n + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
+  const int64_t want = (a.n_frames * std::max(a.nr, a.nc) + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
   int64_t cap = (int64_t)sm_count() * occ;
   if (a.grid_cap > 0 && a.grid_cap < cap) cap = a.grid_cap;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
-  kern<<<grid, TPB, smem, s>>>(code, P, a);
+  kern<<<grid, TPB, smem, s>>>(rowc, colc, P, a);
   return cudaGetLastError();
 }
 
@@ -779,11 +794,12 @@ cudaError_t launch_product_mixed(const MixArgs &m, const MixGroup *host_groups, 
                                                cudaStream_t);                                                    \
   template cudaError_t launch_trace<NPL, SYN>(const DevCode &, const float *, int, uint64_t *, int32_t *,        \
                                               int32_t *, cudaStream_t);                                          \
-  template cudaError_t launch_product_half<NPL, SYN>(const DevCode &, const SisoParams &, const ProductArgs &,   \
-                                                     int, cudaStream_t);                                         \
-  template cudaError_t launch_product_check<NPL, SYN>(const DevCode &, const ProductArgs &, int, cudaStream_t); \
+  template cudaError_t launch_product_half<NPL, SYN>(const DevCode &, const DevCode &, const SisoParams &,       \
+                                                     const ProductArgs &, int, cudaStream_t);                    \
+  template cudaError_t launch_product_check<NPL, SYN>(const DevCode &, const DevCode &, const ProductArgs &, int, \
+                                                      cudaStream_t);                                             \
   template cudaError_t launch_product_init<NPL, SYN>(const DevCode &, const ProductArgs &, cudaStream_t);           \
-  template cudaError_t launch_product_persistent<NPL, SYN>(const DevCode &, const SisoParams &, const ProductArgs &, \
-                                                           cudaStream_t);
+  template cudaError_t launch_product_persistent<NPL, SYN>(const DevCode &, const DevCode &, const SisoParams &,  \
+                                                           const ProductArgs &, cudaStream_t);
 
 }  // namespace sg

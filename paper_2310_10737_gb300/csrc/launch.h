@@ -29,7 +29,9 @@ struct DecodeArgs {
 // Block-turbo decoding of product codes (plain form: one launch per half).
 struct ProductArgs {
   int64_t n_frames;
-  const float *llr_ch;   // [F][n][n] row-major
+  int32_t nr, nc;        // frame: nc rows of nr bits (nr = row code's n, nc = column code's n)
+  int32_t hbw;           // words of hard decisions kept per frame: max(nr, nc)
+  const float *llr_ch;   // [F][nc][nr] row-major
   float alpha;
   int32_t max_half;      // 2 * max iterations
   float *le;             // [F][n][n] extrinsic state (scratch)
@@ -100,15 +102,19 @@ cudaError_t launch_trace(const DevCode &code, const float *lam, int max_q, uint6
 template <int NPL, class SYN>
 cudaError_t launch_product_init(const DevCode &code, const ProductArgs &a, cudaStream_t s);
 
+// Product launchers take the row code (words of a row half) and the column
+// code (words of a column half); a square product code passes one code twice.
 template <int NPL, class SYN>
-cudaError_t launch_product_half(const DevCode &code, const SisoParams &P, const ProductArgs &a, int half,
-                                cudaStream_t s);
+cudaError_t launch_product_half(const DevCode &rowc, const DevCode &colc, const SisoParams &P, const ProductArgs &a,
+                                int half, cudaStream_t s);
 
 template <int NPL, class SYN>
-cudaError_t launch_product_check(const DevCode &code, const ProductArgs &a, int half, cudaStream_t s);
+cudaError_t launch_product_check(const DevCode &rowc, const DevCode &colc, const ProductArgs &a, int half,
+                                 cudaStream_t s);
 
 template <int NPL, class SYN>
-cudaError_t launch_product_persistent(const DevCode &code, const SisoParams &P, const ProductArgs &a, cudaStream_t s);
+cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, const SisoParams &P,
+                                      const ProductArgs &a, cudaStream_t s);
 
 template <class SYN>
 cudaError_t launch_product_mixed(const MixArgs &m, const MixGroup *host_groups, int epoch_halves, cudaStream_t s);

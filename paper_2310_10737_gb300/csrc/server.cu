@@ -293,6 +293,7 @@ cudaError_t launch(sogrand_server *sv, Pool &p, int64_t total_words) {
   cudaError_t e = cudaMemcpyAsync(p.list, p.h_list, F * sizeof(int32_t), cudaMemcpyHostToDevice, p.stream);
   sg::ProductArgs a{};
   a.n_frames = F;
+  a.nr = a.nc = a.hbw = p.n;
   a.llr_ch = p.llr;
   a.alpha = sv->alpha;
   a.max_half = 2 * sv->max_iter;

@@ -290,3 +290,58 @@ def test_fading_frames_match_oracle_and_paper_regime(env, oracle_lib):
         g = _decode(env, code, lch, L=4, query_cap=10**4, thr=1e-4, alpha=0.5, max_iter=20)
         bler = (g["frames"] != X).reshape(3000, -1).any(axis=1).mean()
         assert golden[ebn0] / 1.7 < bler < golden[ebn0] * 1.7, (ebn0, bler, golden[ebn0])
+
+
+@pytest.mark.parametrize("row,col,ebn0,F", [("ebch_64_57", "ebch_64_51", 3.0, 80), ("ebch_32_26", "ebch_16_11", 3.0, 200),
+                                            ("ebch_16_11", "ebch_32_26", 2.75, 200)])
+def test_non_square_product_codes(env, oracle_lib, row, col, ebn0, F):
+    """Products of different row and column codes (n_col x n_row frames) in the
+    plain, batched and host forms, against the oracle's two-code decoder."""
+    torch, sg = env
+    rc, cc = ebch(row), ebch(col)
+    snr = np.where(np.arange(F) % 3 == 2, ebn0 + 2.0, ebn0)
+    U, X, lch = awgn_frames(rc, F, snr, seed=950 + F, col_code=cc)
+    lch[F // 2, 1, 1] = np.nan
+    cr, ccol = sg.Code.from_linear_code(rc), sg.Code.from_linear_code(cc)
+    d = torch.from_numpy(lch).cuda()
+    outs = []
+    for persistent in (False, True):
+        o = sg.product_decode(cr, d, L=4, query_cap=10**4, alpha=0.5, max_iter=10, col_code=ccol,
+                              persistent=persistent)
+        torch.cuda.synchronize()
+        outs.append({k: v.cpu().numpy() for k, v in o.items() if hasattr(v, "cpu")})
+    for key in ("bits", "half_iters", "status", "queries", "par_queries"):
+        np.testing.assert_array_equal(outs[1][key], outs[0][key], err_msg=key)
+    h = sg.product_decode_host(cr, torch.from_numpy(lch).pin_memory(), L=4, query_cap=10**4, alpha=0.5,
+                               max_iter=10, col_code=ccol)
+    for key in ("bits", "half_iters", "status", "queries"):
+        np.testing.assert_array_equal(h[key], outs[1][key], err_msg=key)
+    g = sg.unpack_bits(outs[1]["bits"], cc.n, rc.n)
+    assert outs[1]["status"][F // 2] == 2
+    r = oracle_lib.product_batch(oracle_lib.OracleCode(rc), lch, L=4, cap=10**4, alpha=0.5, max_iter=10,
+                                 col=oracle_lib.OracleCode(cc))
+    first = r["half_iters"] == 1
+    assert first.any()
+    np.testing.assert_array_equal(outs[1]["half_iters"][first], 1)
+    np.testing.assert_array_equal(outs[1]["queries"][first], r["queries"][first])
+    np.testing.assert_array_equal(g[first], r["bits"][first])
+    ok = np.arange(F) != F // 2
+    assert (g[ok] == r["bits"][ok]).reshape(ok.sum(), -1).all(axis=1).mean() >= 0.97
+    for f in range(F):
+        if f == F // 2:
+            continue
+        B = g[f]
+        valid = not rc.syndrome(B).any() and not cc.syndrome(B.T).any()
+        assert valid == (outs[1]["status"][f] == 0)
+    cr.close()
+    ccol.close()
+
+
+def test_product_codes_of_different_kernel_classes_are_refused(env):
+    torch, sg = env
+    cr, ccol = sg.Code.from_linear_code(ebch("ebch_64_57")), sg.Code.from_linear_code(ebch("ebch_32_26"))
+    d = torch.zeros((2, 32, 64), dtype=torch.float32, device="cuda")
+    with pytest.raises(sg.SograndError):
+        sg.product_decode(cr, d, col_code=ccol)
+    cr.close()
+    ccol.close()
