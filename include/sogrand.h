@@ -209,6 +209,23 @@ int product_decode_persistent(sogrand_code *row_code, const sogrand_code *col_co
                               product_decode_stats *stats, void *stream);
 
 /*
+ * Iterative decoding of the (n^2, n^2 - 2n(n-k)) QC-GLDPC code built on a
+ * component code (Sec. VI, from Lentmaier et al.): the n^2 bits, as an n x n
+ * array X[r][j], form n row words (bit j = X[r][j]) and n wrapped diagonal
+ * words (bit j = X[(d + j) mod n][j]), each a codeword of `code`.  Decoding
+ * is the batched form of product decoding with diagonals in place of
+ * columns: rows in odd halves, diagonals in even halves, L_A = fl32(alpha L_E)
+ * of the other set, a frame stopping once every row and diagonal is a
+ * codeword.  Arguments and outputs as product_decode_persistent with
+ * llr_ch device [n_frames][n][n] (X row-major) and bits the decided array.
+ * The paper decodes this code with alpha = 0.6.  Errors: as
+ * product_decode_persistent.
+ */
+int gldpc_decode(sogrand_code *code, int64_t n_frames, const float *llr_ch, int L, int64_t query_cap, float thr,
+                 float alpha, int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
+                 product_decode_stats *stats, void *stream);
+
+/*
  * Schedule of a code's decoding kernels: the number of resident blocks per SM
  * (128 threads each) they are compiled for, 6 (80 registers a thread) or 8
  * (64 registers).  Which is faster depends on the code (register pressure of

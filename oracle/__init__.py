@@ -11,5 +11,5 @@ membership, the complement identity of the remaining mass, the closed form of
 the L=1 corollary and the APP normalisation.
 """
 from .oracle import (  # noqa: F401
-    OracleCode, build, lib, one_line_c, product, product_batch, siso, siso_batch, trace,
+    OracleCode, build, gldpc, gldpc_batch, lib, one_line_c, product, product_batch, siso, siso_batch, trace,
 )

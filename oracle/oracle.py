@@ -54,6 +54,8 @@ def lib():
                                           C.c_double, C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p]
             L.oracle_product2.restype = C.c_int
+            L.oracle_gldpc.argtypes = L.oracle_product.argtypes
+            L.oracle_gldpc.restype = C.c_int
             _lib = L
     return _lib
 
@@ -157,6 +159,36 @@ def product(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20
                           _ptr(bits), _ptr(hi), _ptr(st), _ptr(q), _ptr(qp))
     return dict(bits=bits.reshape(nc, nr), half_iters=int(hi[0]), status=int(st[0]), queries=int(q[0]),
                 par_queries=int(qp[0]))
+
+
+def gldpc(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20) -> dict:
+    """One frame [n, n] of the QC-GLDPC code of component `oc` (rows and wrapped diagonals)."""
+    n = oc.n
+    lch = np.ascontiguousarray(lch, dtype=np.float32).reshape(n * n)
+    bits = np.zeros(n * n, np.uint8)
+    hi = np.zeros(1, np.int32)
+    st = np.zeros(1, np.uint8)
+    q = np.zeros(1, np.int64)
+    qp = np.zeros(1, np.int64)
+    lib().oracle_gldpc(C.byref(oc._s), _ptr(lch), L, cap, thr, C.c_float(alpha), max_iter, _ptr(bits), _ptr(hi),
+                       _ptr(st), _ptr(q), _ptr(qp))
+    return dict(bits=bits.reshape(n, n), half_iters=int(hi[0]), status=int(st[0]), queries=int(q[0]),
+                par_queries=int(qp[0]))
+
+
+def gldpc_batch(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20, threads=None) -> dict:
+    lch = np.ascontiguousarray(lch, dtype=np.float32)
+    F = lch.shape[0]
+    res = [None] * F
+
+    def one(i):
+        res[i] = gldpc(oc, lch[i], L, cap, thr, alpha, max_iter)
+
+    with ThreadPoolExecutor(_threads(threads)) as ex:
+        list(ex.map(one, range(F)))
+    return dict(bits=np.stack([r["bits"] for r in res]), half_iters=np.array([r["half_iters"] for r in res]),
+                status=np.array([r["status"] for r in res]), queries=np.array([r["queries"] for r in res]),
+                par_queries=np.array([r["par_queries"] for r in res]))
 
 
 def product_batch(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20, threads=None,

@@ -546,14 +546,23 @@ int oracle_siso(const oracle_code *code, const float *lch, const float *la, int 
 /* ------------------------------------------------------------------ */
 /* product codes: block turbo decoding (Sec. VI, Fig. turboDec)         */
 /* ------------------------------------------------------------------ */
-/* every row of the n_col x n_row frame is a row-code word and every column a column-code word */
-static int frame_valid(const oracle_code *row, const oracle_code *col, const uint8_t *B, uint8_t *tmp)
+/* Position of bit i of word w of the second set of checks: column w of the
+   n_col x n_row frame (product code), or wrapped diagonal w of the n x n
+   array (QC-GLDPC: bit i is X[(w + i) mod n][i]). */
+static size_t second_pos(int diag, int nr, int w, int i)
+{
+    return diag ? (size_t)((w + i) % nr) * nr + i : (size_t)i * nr + w;
+}
+
+/* every row of the frame is a row-code word and every word of the second set
+   (columns, or wrapped diagonals) a column-code word */
+static int frame_valid(const oracle_code *row, const oracle_code *col, int diag, const uint8_t *B, uint8_t *tmp)
 {
     int nr = row->n, nc = col->n;
     for (int i = 0; i < nc; i++)
         if (!is_codeword(row, B + (size_t)i * nr)) return 0;
-    for (int j = 0; j < nr; j++) {
-        for (int i = 0; i < nc; i++) tmp[i] = B[(size_t)i * nr + j];
+    for (int w = 0; w < nr; w++) {
+        for (int i = 0; i < nc; i++) tmp[i] = B[second_pos(diag, nr, w, i)];
         if (!is_codeword(col, tmp)) return 0;
     }
     return 1;
@@ -569,9 +578,9 @@ static int frame_valid(const oracle_code *row, const oracle_code *col, const uin
  * status (0 decoded, 1 max iterations, 2 invalid input), total queries and
  * the "parallelized" count (sum over halves of the max per-word queries).
  */
-int oracle_product2(const oracle_code *row, const oracle_code *col, const float *lch, int L, int64_t cap,
-                    double thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status,
-                    int64_t *queries, int64_t *par_queries)
+static int product_core(const oracle_code *row, const oracle_code *col, int diag, const float *lch, int L,
+                        int64_t cap, double thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                        uint8_t *status, int64_t *queries, int64_t *par_queries)
 {
     int nr = row->n, nc = col->n;
     size_t nn = (size_t)nr * nc;
@@ -591,7 +600,7 @@ int oracle_product2(const oracle_code *row, const oracle_code *col, const float 
         int64_t qmax = 0;
         for (int w = 0; w < nw; w++) {
             for (int i = 0; i < len; i++) {
-                size_t pos = rows ? (size_t)w * nr + i : (size_t)i * nr + w;
+                size_t pos = rows ? (size_t)w * nr + i : second_pos(diag, nr, w, i);
                 wl[i] = lch[pos];
                 wa[i] = alpha * LE[pos]; /* FP32 product, no contraction */
             }
@@ -604,13 +613,13 @@ int oracle_product2(const oracle_code *row, const oracle_code *col, const float 
             qsum += q;
             if (q > qmax) qmax = q;
             for (int i = 0; i < len; i++) {
-                size_t pos = rows ? (size_t)w * nr + i : (size_t)i * nr + w;
+                size_t pos = rows ? (size_t)w * nr + i : second_pos(diag, nr, w, i);
                 LE[pos] = (float)lext[i];
                 B[pos] = hd[i];
             }
         }
         qpar += qmax;
-        if (frame_valid(row, col, B, tmp)) {
+        if (frame_valid(row, col, diag, B, tmp)) {
             st = 0;
             break;
         }
@@ -625,6 +634,26 @@ done:
     free(LE);
     free(B);
     return 0;
+}
+
+/* product of a row code and a column code (an n_col x n_row frame) */
+int oracle_product2(const oracle_code *row, const oracle_code *col, const float *lch, int L, int64_t cap,
+                    double thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status,
+                    int64_t *queries, int64_t *par_queries)
+{
+    return product_core(row, col, 0, lch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
+                        par_queries);
+}
+
+/* QC-GLDPC of a component code (Sec. VI): rows and wrapped diagonals of an
+   n x n array, decoded alternately like the rows and columns of a product
+   code, the iteration stopping once every row and diagonal is a codeword */
+int oracle_gldpc(const oracle_code *code, const float *lch, int L, int64_t cap, double thr, float alpha,
+                 int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
+                 int64_t *par_queries)
+{
+    return product_core(code, code, 1, lch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
+                        par_queries);
 }
 
 /* square product code: the same code on rows and columns */

@@ -66,6 +66,7 @@ def load() -> C.CDLL:
                                                 C.POINTER(ProductStats), vp]
         L.sogrand_trace_patterns.argtypes = [vp, vp, i64, vp, C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
         L.sogrand_release_cached.argtypes = []
+        L.gldpc_decode.argtypes = [vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, C.POINTER(ProductStats), vp]
         L.sogrand_server_create.argtypes = [i32, C.POINTER(vp), C.POINTER(C.c_int64), i32, i64, f32, f32, i32, i32,
                                             C.POINTER(vp)]
         L.sogrand_server_submit.argtypes = [vp, i32, i64, vp, vp, vp, vp, vp, C.POINTER(C.c_int64)]
@@ -85,6 +86,7 @@ def load() -> C.CDLL:
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
                      "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak",
                      "product_decode_mixed", "sogrand_code_schedule", "sogrand_code_tune", "sogrand_server_create",
+                     "gldpc_decode",
                      "sogrand_server_submit", "sogrand_server_wait", "sogrand_server_stats", "sogrand_server_destroy"):
             getattr(L, name).restype = C.c_int
         _lib = L
@@ -237,6 +239,28 @@ def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: 
     if stats:
         out["timing_ms"] = (float(tm[0]), float(tm[1]))
         out["launches"] = int(ln[0])
+    return out
+
+
+def gldpc_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.6,
+                 max_iter: int = 20, stream=None) -> dict:
+    """QC-GLDPC frames [F, n, n] (rows and wrapped diagonals are component words); returns CUDA tensors."""
+    import torch
+    F, n, n2 = llr_ch.shape
+    assert n == n2 == code.n and llr_ch.is_cuda and llr_ch.dtype == torch.float32 and llr_ch.is_contiguous()
+    dev = llr_ch.device
+    out = dict(bits=torch.empty((F, (n * n + 7) // 8), dtype=torch.uint8, device=dev),
+               half_iters=torch.empty(F, dtype=torch.int32, device=dev),
+               status=torch.empty(F, dtype=torch.uint8, device=dev),
+               queries=torch.empty(F, dtype=torch.int64, device=dev),
+               par_queries=torch.empty(F, dtype=torch.int64, device=dev))
+    tm = (C.c_float * 2)()
+    st = ProductStats(_ptr(out["par_queries"]), None, None, C.cast(tm, C.POINTER(C.c_float)), None)
+    rc = load().gldpc_decode(code.handle, F, _ptr(llr_ch), int(L), int(query_cap), float(thr), float(alpha),
+                             int(max_iter), _ptr(out["bits"]), _ptr(out["half_iters"]), _ptr(out["status"]),
+                             _ptr(out["queries"]), C.byref(st), _stream(stream))
+    _check(rc, "gldpc_decode")
+    out["timing_ms"] = float(tm[0])
     return out
 
 

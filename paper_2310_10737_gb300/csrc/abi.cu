@@ -663,7 +663,7 @@ size_t persistent_scratch_bytes(int64_t F, int nr, int nc, int nm, int max_iter)
 cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t F, const float *llr_ch,
                                const sg::SisoParams &P, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
                                uint8_t *status, int64_t *queries, int64_t *par_queries, unsigned long long *wsum,
-                               int32_t *xf, char *mem, cudaStream_t s, int32_t **err_dev) {
+                               int32_t *xf, char *mem, cudaStream_t s, int32_t **err_dev, int diag = 0) {
   const int nr = c->n, nc = cc->n, nm = c->nm, hbw = std::max(nr, nc);
   char *p = mem;
   auto take = [&p](size_t bytes) {
@@ -677,6 +677,7 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   a.nr = nr;
   a.nc = nc;
   a.hbw = hbw;
+  a.diag = diag;
   a.llr_ch = llr_ch;
   a.alpha = alpha;
   a.max_half = 2 * max_iter;
@@ -711,9 +712,13 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
 
 extern "C" {
 
-int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
-                              int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
-                              uint8_t *status, int64_t *queries, product_decode_stats *stats, void *stream) {
+}  // extern "C"
+
+namespace {
+// The batched form for a product code (diag = 0) or a QC-GLDPC (diag = 1).
+int persistent_decode(sogrand_code *rc_, const sogrand_code *cc_, int diag, int64_t F, const float *llr_ch, int L,
+                      int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                      uint8_t *status, int64_t *queries, product_decode_stats *stats, void *stream) {
   if (stats && stats->timing_ms) stats->timing_ms[0] = stats->timing_ms[1] = 0.f;
   if (stats && stats->launches) stats->launches[0] = 0;
   int rc = persistent_check(rc_, cc_, F, L, cap, thr, alpha, max_iter);
@@ -740,7 +745,7 @@ int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_
     e = persistent_enqueue(c, cc, F, llr_ch, P, alpha, max_iter, bits, half_iters, status, queries,
                            stats ? stats->par_queries : nullptr,
                            stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr,
-                           stats ? stats->xf_words : nullptr, mem, s, &err_dev);
+                           stats ? stats->xf_words : nullptr, mem, s, &err_dev, diag);
   if (e == cudaSuccess && timed) e = cudaEventRecord(ev[1], s);
   int32_t err = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&err, err_dev, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
@@ -756,6 +761,23 @@ int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_
   cudaError_t e2 = cudaFreeAsync(mem, s);
   if (e != cudaSuccess || e2 != cudaSuccess) return SOGRAND_ECUDA;
   return err ? SOGRAND_ETIMEOUT : SOGRAND_OK;
+}
+}  // namespace
+
+extern "C" {
+
+int product_decode_persistent(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, const float *llr_ch, int L,
+                              int64_t cap, float thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
+                              uint8_t *status, int64_t *queries, product_decode_stats *stats, void *stream) {
+  return persistent_decode(rc_, cc_, 0, F, llr_ch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
+                           stats, stream);
+}
+
+int gldpc_decode(sogrand_code *code, int64_t F, const float *llr_ch, int L, int64_t cap, float thr, float alpha,
+                 int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries,
+                 product_decode_stats *stats, void *stream) {
+  return persistent_decode(code, code, 1, F, llr_ch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
+                           stats, stream);
 }
 
 int sogrand_code_schedule(sogrand_code *c, int minb, int *current) {

@@ -171,7 +171,8 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     const int i = lane + 32 * k;
     float x = 0.f;
     if (i < n) {
-      const size_t pos = fb + (rows ? (size_t)wd * nr + i : (size_t)i * nr + wd);
+      const size_t pos = fb + (rows ? (size_t)wd * nr + i
+                                    : (a.diag ? (size_t)((wd + i) % nr) * nr + i : (size_t)i * nr + wd));
       x = __ldg(a.llr_ch + pos);
       if (half > 1) x = __fadd_rn(x, __fmul_rn(a.alpha, ld_state<COHERENT>(a.le + pos)));  // L_A = alpha L_E
     }
@@ -187,7 +188,8 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
   for (int k = 0; k < NPL; k++) {
     const int i = lane + 32 * k;
     if (i < n) {
-      const size_t pos = fb + (rows ? (size_t)wd * nr + i : (size_t)i * nr + wd);
+      const size_t pos = fb + (rows ? (size_t)wd * nr + i
+                                    : (a.diag ? (size_t)((wd + i) % nr) * nr + i : (size_t)i * nr + wd));
       a.le[pos] = (empty || res.queries < 0) ? 0.f : __fsub_rn(lapp[k], lam[k]);
     }
     hb[k] = __ballot_sync(FULL, i < n && lapp[k] < 0.f);
@@ -265,9 +267,41 @@ __device__ __forceinline__ bool frame_valid(const DevCode &wc, const DevCode &xc
   return ok;
 }
 
+// QC-GLDPC frame check: W holds the n words of the last half (rows, or the
+// wrapped diagonals after a diagonal half).  Each must be a codeword, and so
+// must each word of the other set, whose syndrome is gathered bit by bit:
+// after a row half diagonal x has bit j = bit j of row (x + j) mod n; after a
+// diagonal half row x has bit j = bit j of diagonal (x - j) mod n.
+template <int NPL>
+__device__ __forceinline__ bool frame_valid_diag(const DevCode &code, const uint64_t *W, bool rows, int lane) {
+  constexpr int NM = (32 * NPL + 63) / 64;
+  const int n = code.n;
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < NPL; k++) {
+    const int x = lane + 32 * k;
+    if (x < n) {
+      for (int t = 0; t < code.m && ok; t++) {
+        int p = 0;
+#pragma unroll
+        for (int y = 0; y < NM; y++) p ^= __popcll(W[x * NM + y] & __ldg(code.hrow + t * NM + y));
+        if (p & 1) ok = false;
+      }
+      uint64_t syn = 0;
+      for (int j = 0; j < n; j++) {
+        const int w = rows ? (x + j) % n : (x - j + n) % n;
+        if ((W[w * NM + (j >> 6)] >> (j & 63)) & 1ull) syn ^= __ldg(code.hcol + j);
+      }
+      if (syn) ok = false;
+    }
+  }
+  return __all_sync(FULL, ok);
+}
+
 // Write the frame's decision as row-major bits and its status.  W holds the
-// words of the last half: rows (bit j of word i is bit (i, j)) or columns
-// (bit i of word j is bit (i, j)).
+// words of the last half: rows (bit j of word i is bit (i, j)), columns
+// (bit i of word j is bit (i, j)) or, for a QC-GLDPC, wrapped diagonals (bit j
+// of word (i - j) mod n is bit (i, j)).
 template <int NPL>
 __device__ __forceinline__ void frame_finish(const ProductArgs &a, int64_t f, bool rows, int half, int status,
                                              const uint64_t *W, int lane) {
@@ -282,7 +316,9 @@ __device__ __forceinline__ void frame_finish(const ProductArgs &a, int64_t f, bo
       const int p = by * 8 + t;
       if (p < nbits) {
         const int i = p / nr, j = p - i * nr;
-        const uint64_t word = rows ? W[i * NM + (j >> 6)] >> (j & 63) : W[j * NM + (i >> 6)] >> (i & 63);
+        const uint64_t word = rows     ? W[i * NM + (j >> 6)] >> (j & 63)
+                              : a.diag ? W[((i - j + nr) % nr) * NM + (j >> 6)] >> (j & 63)
+                                       : W[j * NM + (i >> 6)] >> (i & 63);
         v |= (unsigned)(word & 1ull) << t;
       }
     }
@@ -341,7 +377,7 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode rowc, const
     uint64_t *W = words_s[warp];
     for (int x = lane; x < n * NM; x += 32) W[x] = a.hb[(size_t)f * a.hbw * NM + x];
     __syncwarp();
-    const bool ok = frame_valid<NPL>(wc, xc, W, lane);
+    const bool ok = a.diag ? frame_valid_diag<NPL>(wc, W, rows, lane) : frame_valid<NPL>(wc, xc, W, lane);
     const bool bad = st == F_BAD_PENDING;
     const bool finish = bad || ok || half >= a.max_half;
     if (lane == 0) {
@@ -422,7 +458,7 @@ __device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCod
   const bool rows = (half & 1) != 0;
   for (int x = lane; x < n * NM; x += 32) W[x] = ld_state<true>(a.hb + (size_t)f * a.hbw * NM + x);
   __syncwarp();
-  const bool ok = frame_valid<NPL>(wc, xc, W, lane);
+  const bool ok = a.diag ? frame_valid_diag<NPL>(wc, W, rows, lane) : frame_valid<NPL>(wc, xc, W, lane);
   int bad = 0, stop = 0;
   if (lane == 0) {
     bad = __ldcg(a.bad + f);

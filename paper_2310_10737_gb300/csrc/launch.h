@@ -31,6 +31,8 @@ struct ProductArgs {
   int64_t n_frames;
   int32_t nr, nc;        // frame: nc rows of nr bits (nr = row code's n, nc = column code's n)
   int32_t hbw;           // words of hard decisions kept per frame: max(nr, nc)
+  int32_t diag;          // 1: QC-GLDPC, the second set of words are the wrapped diagonals of the n x n frame
+                         // (bit i of word w is bit ((w + i) mod n, i)) instead of its columns
   const float *llr_ch;   // [F][nc][nr] row-major
   float alpha;
   int32_t max_half;      // 2 * max iterations
