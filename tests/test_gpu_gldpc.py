@@ -39,7 +39,7 @@ def _decode(env, code, lch, **kw):
 def test_gldpc_matches_the_oracle(env, oracle_lib, comp, ebn0, F):
     code = ebch(comp)
     g = QCGLDPC(code)
-    snr = np.where(np.arange(F) % 4 == 3, ebn0 + 1.5, ebn0)
+    snr = np.where(np.arange(F) % 3 == 2, 5.5, ebn0)  # a third at 5.5 dB: about half of those stop after one half
     U, X, lch = gldpc_frames(g, F, snr, seed=1200 + F)
     bad = F // 3
     lch[bad, 2, 5] = np.inf
