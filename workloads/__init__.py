@@ -12,7 +12,7 @@ It holds none of the decoding arithmetic (no query order, no soft output), so
 the oracle and the GPU path can both consume its outputs without sharing any
 of the method's code.
 """
-from .codes import LinearCode, ebch, CODE_SPECS  # noqa: F401
+from .codes import LinearCode, ebch, shorten, CODE_SPECS  # noqa: F401
 from .channel import awgn_frames, awgn_words, sigma2_for  # noqa: F401
 from .fading import fading_frames  # noqa: F401
 from .gldpc import QCGLDPC, gldpc_frames  # noqa: F401

@@ -65,24 +65,33 @@ def _generate(code, count, ebn0_db, seed, stream, first, nbits_info, nbits, rate
 
 
 def awgn_frames(code, count: int, ebn0_db, seed: int, first: int = 0, stream: int = 1, threads: int | None = None,
-                col_code=None):
+                col_code=None, punctured=None):
     """Product-code frames: (U [F,k,k] u8, X [F,n,n] u8, L_Ch [F,n,n] f32).
 
     ``ebn0_db`` is a scalar or one value per frame; the rate is the product
     code's k^2/n^2.  With ``col_code`` the frames are of the product of the
     row code ``code`` and the column code: U [F,k_col,k_row], X and L_Ch
-    [F,n_col,n_row], rate k_row k_col / (n_row n_col).
+    [F,n_col,n_row], rate k_row k_col / (n_row n_col).  ``punctured`` (a 0/1
+    mask of the frame's shape) marks coded bits that are not transmitted:
+    their L_Ch is 0 (an erasure) and the rate counts only the sent bits.
     """
+    r, c = code, (code if col_code is None else col_code)
+    nbits = r.n * c.n
+    sent = nbits if punctured is None else nbits - int(np.count_nonzero(punctured))
+    if punctured is not None and np.shape(punctured) != (c.n, r.n):
+        raise ValueError("punctured must have the frame's shape [n_col, n_row]")
     if col_code is None:
         n, k = code.n, code.k
-        U, X, L = _generate(code, count, ebn0_db, seed, stream, first, k * k, n * n, (k * k) / (n * n),
+        U, X, L = _generate(code, count, ebn0_db, seed, stream, first, k * k, nbits, (k * k) / sent,
                             lambda u: code.product_encode(u.reshape(-1, k, k)), threads)
-        return U.reshape(-1, k, k), X.reshape(-1, n, n), L.reshape(-1, n, n)
-    from .codes import product_encode
-    r, c = code, col_code
-    U, X, L = _generate(code, count, ebn0_db, seed, stream, first, r.k * c.k, r.n * c.n, (r.k * c.k) / (r.n * c.n),
-                        lambda u: product_encode(r, c, u.reshape(-1, c.k, r.k)), threads)
-    return U.reshape(-1, c.k, r.k), X.reshape(-1, c.n, r.n), L.reshape(-1, c.n, r.n)
+    else:
+        from .codes import product_encode
+        U, X, L = _generate(code, count, ebn0_db, seed, stream, first, r.k * c.k, nbits, (r.k * c.k) / sent,
+                            lambda u: product_encode(r, c, u.reshape(-1, c.k, r.k)), threads)
+    L = L.reshape(-1, c.n, r.n)
+    if punctured is not None:
+        L[:, np.asarray(punctured, dtype=bool)] = 0.0
+    return U.reshape(-1, c.k, r.k), X.reshape(-1, c.n, r.n), L
 
 
 def awgn_words(code, count: int, ebn0_db, seed: int, first: int = 0, stream: int = 2, threads: int | None = None):

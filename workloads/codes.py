@@ -167,6 +167,21 @@ def product_encode(row: LinearCode, col: LinearCode, U: np.ndarray) -> np.ndarra
     return np.ascontiguousarray(cols.reshape(F, row.n, col.n).transpose(0, 2, 1))
 
 
+def shorten(code: LinearCode, s: int) -> LinearCode:
+    """The (n - s, k - s) code of `code` (systematic, G = [I_k | P]) shortened
+    by its first s information positions: codewords of `code` that are zero
+    there, with those positions deleted (G' = G[s:, s:], H' = H[:, s:]).  An
+    even code stays even (its all-ones check restricted to the kept positions).
+    Rate adaptation of product codes by shortening (Sec. VII) uses such
+    components."""
+    if not 0 <= s < code.k:
+        raise ValueError("0 <= s < k")
+    if not (code.G[:, :code.k] == np.eye(code.k, dtype=np.uint8)).all():
+        raise ValueError("shortening needs a systematic generator [I_k | P]")
+    return LinearCode(name=f"{code.name}_s{s}", n=code.n - s, k=code.k - s,
+                      G=np.ascontiguousarray(code.G[s:, s:]), H=np.ascontiguousarray(code.H[:, s:]), even=code.even)
+
+
 def ebch(name_or_nk) -> LinearCode:
     """Extended BCH code by name ('ebch_64_57') or by (n, k)."""
     if isinstance(name_or_nk, tuple):
