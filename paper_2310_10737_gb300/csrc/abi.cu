@@ -369,7 +369,7 @@ cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P
                                   cudaStream_t s) {
   const sg::DevCode d = dev_code(c);
   cudaError_t e = cudaSuccess;
-  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, d, P, a, s)));
+  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN, false>(d, d, P, a, s)));
   return e;
 }
 int sm_count_of_device() {
@@ -580,6 +580,7 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   a.xf_count = stats ? stats->xf_words : nullptr;
   a.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
   sg::DevCode d = dev_code(c), dcol = dev_code(cc);
+  const bool gen = cc != c || a.nr != a.nc;  // not the square product of one code
   sg::SisoParams P{L, (int32_t)cap, thr};
   cudaError_t e = cudaSuccess;
   const bool timed = stats && stats->timing_ms;
@@ -591,7 +592,9 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_init<NPL, SYN>(d, a, s)));
   for (int h = 1; h <= a.max_half && e == cudaSuccess; h++) {
     if (timed) e = cudaEventRecord(ev[0], s);
-    if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, dcol, P, a, h, s)));
+    if (e == cudaSuccess)
+      SG_DISPATCH(c, e = (gen ? sg::launch_product_half<NPL, SYN, true>(d, dcol, P, a, h, s)
+                              : sg::launch_product_half<NPL, SYN, false>(d, dcol, P, a, h, s)));
     if (e != cudaSuccess) break;
     launches++;
     if (timed) e = cudaEventRecord(ev[1], s);
@@ -703,8 +706,10 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   a.wsum = wsum;
   *err_dev = a.ctrl + 3;
   sg::DevCode d = dev_code(c), dcol = dev_code(cc);
+  const bool gen = cc != c || a.diag || a.nr != a.nc;  // not the square product of one code
   cudaError_t e = cudaSuccess;
-  SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN>(d, dcol, P, a, s)));
+  SG_DISPATCH(c, e = (gen ? sg::launch_product_persistent<NPL, SYN, true>(d, dcol, P, a, s)
+                          : sg::launch_product_persistent<NPL, SYN, false>(d, dcol, P, a, s)));
   return e;
 }
 
@@ -1178,7 +1183,7 @@ int product_decode_noalloc(sogrand_code *rc_, const sogrand_code *cc_, int64_t F
   // every half iteration is launched; the kernels skip frames that finished,
   // so the host never waits on the device
   for (int h = 1; h <= a.max_half && e == cudaSuccess; h++) {
-    SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN>(d, d, P, a, h, s)));
+    SG_DISPATCH(c, e = (sg::launch_product_half<NPL, SYN, false>(d, d, P, a, h, s)));
     if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, d, a, h, s)));
   }
   return e == cudaSuccess ? SOGRAND_OK : SOGRAND_ECUDA;

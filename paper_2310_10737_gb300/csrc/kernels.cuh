@@ -76,7 +76,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const 
       const int i = lane + 32 * k;
       if (i < n) {
         if (a.llr_app) a.llr_app[base + i] = lapp[k];
-        if (a.llr_ext) a.llr_ext[base + i] = empty ? 0.f : __fsub_rn(lapp[k], lam[k]);
+        if (a.llr_ext) a.llr_ext[base + i] = empty ? 0.f : __fsub_rn(lapp[k], sc.lam_at(i));
         if (a.hard) a.hard[base + i] = lapp[k] < 0.f ? 1 : 0;
       }
     }
@@ -137,34 +137,46 @@ __device__ __forceinline__ uint64_t ld_state(const uint64_t *p) {
   return *p;
 }
 
-// Per-warp tallies flushed to the global counters once, when the warp exits.
-struct WarpTally {
-  unsigned long long wsum = 0;  // summed pattern weights
-  int xf = 0;                   // words that took the extended-range path
-  __device__ void flush(const ProductArgs &a, int lane) const {
-    if (lane != 0) return;
-    if (a.wsum && wsum) atomicAdd(a.wsum, wsum);
-    if (a.xf_count && xf) atomicAdd(a.xf_count, xf);
-  }
+// Per-warp tallies live in the warp's shared slot (not in registers, which
+// the search needs) and reach the global counters once, when the warp exits.
+__device__ __forceinline__ void tally_clear(unsigned long long *slot, int lane) {
+  if (lane == 0) slot[0] = slot[1] = 0ull;
+  __syncwarp();
+}
+__device__ __forceinline__ void tally_flush(const unsigned long long *slot, unsigned long long *wsum, int32_t *xf_count,
+                                            int lane) {
+  __syncwarp();
+  if (lane != 0) return;
+  if (wsum && slot[0]) atomicAdd(wsum, slot[0]);
+  if (xf_count && slot[1]) atomicAdd(xf_count, (int32_t)slot[1]);
+}
+
+// The words' context (frame, word, half, list index) is kept in the frame
+// check area sc.W(), which nothing uses during a word, and read back after
+// the search: the registers that held it are free while the search runs.
+struct WordCtx {
+  int64_t f, li;
+  int32_t wd, half;
 };
 
 // One component word of frame f in half `half` (rows when odd): lambda =
 // L_Ch + fl32(alpha L_E) (L_A = 0 in the first half), SOGRAND, then L_E and
 // the hard decision of L_APP are stored and the query counters updated.
 // `code` is the code of this half's words (the row code in a row half, the
-// column code in a column half); the frame is a.nc rows of a.nr bits.
+// column code in a column half).  GEN: the frame is a.nc rows of a.nr bits
+// and the second set of words may be wrapped diagonals (a.diag); otherwise
+// it is a square code.n x code.n frame with columns as the second set.
 // Returns the word's query count (-1: non-finite input).
-template <int NPL, class SYN, bool COHERENT>
+template <int NPL, class SYN, bool COHERENT, bool GEN>
 __device__ __forceinline__ int product_word(const DevCode &code, const SisoParams &P, const ProductArgs &a,
-                                            const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane,
-                                            WarpTally &tally) {
+                                            const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
 #ifdef SG_PHASE_PROFILE
   const long long t0 = clock64();
 #endif
-  const int n = code.n, nr = a.nr;
-  const bool rows = (half & 1) != 0;
-  const size_t fb = (size_t)f * nr * a.nc;
+  const int n = code.n, nr = GEN ? a.nr : n;
+  const bool rows = (half & 1) != 0, diag = GEN && a.diag;
+  const size_t fb = (size_t)f * nr * (GEN ? a.nc : n);
   float lam[NPL];
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
@@ -172,7 +184,7 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     float x = 0.f;
     if (i < n) {
       const size_t pos = fb + (rows ? (size_t)wd * nr + i
-                                    : (a.diag ? (size_t)((wd + i) % nr) * nr + i : (size_t)i * nr + wd));
+                                    : (diag ? (size_t)((wd + i) % nr) * nr + i : (size_t)i * nr + wd));
       x = __ldg(a.llr_ch + pos);
       if (half > 1) x = __fadd_rn(x, __fmul_rn(a.alpha, ld_state<COHERENT>(a.le + pos)));  // L_A = alpha L_E
     }
@@ -181,21 +193,36 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
   float lapp[NPL];
   WordResult res;
   int used_xf = 0;
+  WordCtx *ctx = reinterpret_cast<WordCtx *>(sc.W());
+  if (lane == 0) {
+    ctx->f = f;
+    ctx->wd = wd;
+    ctx->half = half;
+  }
+  __syncwarp();
   siso_word<NPL, SYN>(code, P, sc, lam, lane, lapp, res, &used_xf);
+  bool rows2;
+  {
+    const volatile WordCtx *vc = ctx;
+    f = vc->f;
+    wd = vc->wd;
+    rows2 = (vc->half & 1) != 0;
+  }
+  const size_t fb2 = (size_t)f * nr * (GEN ? a.nc : n);
   const bool empty = res.nhit == 0;
   unsigned hb[NPL];
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
     const int i = lane + 32 * k;
     if (i < n) {
-      const size_t pos = fb + (rows ? (size_t)wd * nr + i
-                                    : (a.diag ? (size_t)((wd + i) % nr) * nr + i : (size_t)i * nr + wd));
-      a.le[pos] = (empty || res.queries < 0) ? 0.f : __fsub_rn(lapp[k], lam[k]);
+      const size_t pos = fb2 + (rows2 ? (size_t)wd * nr + i
+                                     : (diag ? (size_t)((wd + i) % nr) * nr + i : (size_t)i * nr + wd));
+      a.le[pos] = (empty || res.queries < 0) ? 0.f : __fsub_rn(lapp[k], sc.lam_at(i));
     }
     hb[k] = __ballot_sync(FULL, i < n && lapp[k] < 0.f);
   }
   if (lane == 0) {
-    uint64_t *dst = a.hb + ((size_t)f * a.hbw + wd) * NM;
+    uint64_t *dst = a.hb + ((size_t)f * (GEN ? a.hbw : n) + wd) * NM;
 #pragma unroll
     for (int wd2 = 0; wd2 < NM; wd2++) {
       uint64_t v = hb[2 * wd2];
@@ -205,9 +232,9 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     if (res.queries >= 0) {
       atomicAdd(reinterpret_cast<unsigned long long *>(a.queries + f), (unsigned long long)res.queries);
       atomicMax(a.hmax + f, res.queries);
-      tally.wsum += (unsigned long long)res.wsum;
+      sc.tally()[0] += (unsigned long long)res.wsum;
     }
-    tally.xf += used_xf & 1;
+    sc.tally()[1] += used_xf & 1;
     if ((used_xf & 2) && a.ctrl) atomicExch(a.ctrl + 3, 2);  // stops a persistent launch: reported as a timeout
   }
   __syncwarp();
@@ -332,7 +359,7 @@ __device__ __forceinline__ void frame_finish(const ProductArgs &a, int64_t f, bo
 }
 
 // ---- plain form: one launch per half iteration, then a check launch ----
-template <int NPL, class SYN, bool ROWS, int MINB>
+template <int NPL, class SYN, bool ROWS, int MINB, bool GEN>
 __global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode rowc, const DevCode colc, const SisoParams P,
                                                          const ProductArgs a, int half) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -346,17 +373,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode rowc, 
   const int n = ROWS ? a.nc : a.nr;          // words per frame in this half
   const int64_t items = a.n_frames * n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
-  WarpTally tally;
+  tally_clear(sc.tally(), lane);
   for (int64_t it = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp; it < items; it += nwarps) {
     const int64_t f = it / n;
     const int wd = (int)(it - f * n);
     const int32_t fs = __ldg(a.fstate + f);
     if (fs != F_RUN && fs != F_BAD_PENDING) continue;  // finished frames only: a flag raised during
                                                         // this half must not change which words run
-    const int q = product_word<NPL, SYN, false>(code, P, a, sc, f, wd, half, lane, tally);
+    const int q = product_word<NPL, SYN, false, GEN>(code, P, a, sc, f, wd, half, lane);
     if (lane == 0 && q < 0) atomicExch(a.fstate + f, (int32_t)F_BAD_PENDING);
   }
-  tally.flush(a, lane);
+  tally_flush(sc.tally(), a.wsum, a.xf_count, lane);
 }
 
 // One warp per frame.
@@ -448,7 +475,7 @@ __device__ __forceinline__ int sched_take(int32_t *ctrl_w, const volatile int32_
 // After the last word of a half of frame f (list entry f + 1 in the launch's
 // index space `gf`): check the frame and finish it, park it (a serving epoch
 // ran out: its state stays for the next launch) or append its next half.
-template <int NPL>
+template <int NPL, bool GEN>
 __device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCode &xc, const ProductArgs &a,
                                                  int32_t *ctrl, int32_t *queue_w, int64_t f, int64_t gf, int half,
                                                  uint64_t *W, int lane) {
@@ -456,9 +483,10 @@ __device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCod
   const int n = xc.n;  // words of this half
   __threadfence();
   const bool rows = (half & 1) != 0;
-  for (int x = lane; x < n * NM; x += 32) W[x] = ld_state<true>(a.hb + (size_t)f * a.hbw * NM + x);
+  const int hbw = GEN ? a.hbw : n;
+  for (int x = lane; x < n * NM; x += 32) W[x] = ld_state<true>(a.hb + (size_t)f * hbw * NM + x);
   __syncwarp();
-  const bool ok = a.diag ? frame_valid_diag<NPL>(wc, W, rows, lane) : frame_valid<NPL>(wc, xc, W, lane);
+  const bool ok = (GEN && a.diag) ? frame_valid_diag<NPL>(wc, W, rows, lane) : frame_valid<NPL>(wc, xc, W, lane);
   int bad = 0, stop = 0;
   if (lane == 0) {
     bad = __ldcg(a.bad + f);
@@ -496,8 +524,12 @@ __device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCod
 // either finishes the frame or appends it for its next half.  A warp whose
 // slot is not filled yet waits with exponential back-off; all waits are
 // bounded (a.max_spin microseconds of accumulated sleep without progress):
-// the kernel then records an error and every warp returns.
-template <int NPL, class SYN, int MINB>
+// the kernel then records an error and every warp returns.  GEN: two codes or
+// wrapped diagonals (the code of a word is chosen per half); otherwise a
+// square product code whose words all use rowc, with no per-word selection
+// of a code (selecting one of two parameter structs at run time makes the
+// compiler copy it to local memory).
+template <int NPL, class SYN, int MINB, bool GEN>
 __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode rowc, const DevCode colc,
                                                                const SisoParams P, const ProductArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -507,22 +539,29 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
   init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(jm));
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(jm));
-  const int slot_n = max(a.nr, a.nc);  // tickets per list slot: the larger number of words in a half
+  const int slot_n = GEN ? max(a.nr, a.nc) : rowc.n;  // tickets per list slot: the most words in a half
   const int64_t nslots = a.n_frames * (int64_t)a.max_half;  // a frame has at most max_half halves
-  WarpTally tally;
+  tally_clear(sc.tally(), lane);
   for (;;) {
     int slot, w, f1;
     if (!sched_take(a.ctrl, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1)) break;
-    const int64_t li = (int64_t)f1 - 1;  // list index
-    const int64_t f = a.frame_list ? (int64_t)a.frame_list[li] : li;
+    int64_t li = (int64_t)f1 - 1;  // list index
+    int64_t f = a.frame_list ? (int64_t)a.frame_list[li] : li;
     int half = 0;
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
     const bool rows = (half & 1) != 0;
-    const DevCode &code = rows ? rowc : colc, &xcode = rows ? colc : rowc;
+    const DevCode &code = GEN ? (rows ? rowc : colc) : rowc, &xcode = GEN ? (rows ? colc : rowc) : rowc;
     const int n = xcode.n;  // words in this half
-    if (w >= n) continue;   // a ticket past this half's words (codes of different lengths)
-    const int q = product_word<NPL, SYN, true>(code, P, a, sc, f, w, half, lane, tally);
+    if (GEN && w >= n) continue;  // a ticket past this half's words (codes of different lengths)
+    if (lane == 0) reinterpret_cast<WordCtx *>(sc.W())->li = li;
+    const int q = product_word<NPL, SYN, true, GEN>(code, P, a, sc, f, w, half, lane);
+    {
+      const volatile WordCtx *vc = reinterpret_cast<const volatile WordCtx *>(sc.W());
+      f = vc->f;
+      li = vc->li;
+      half = vc->half;
+    }
     if (lane == 0 && q < 0) atomicExch(a.bad + f, 1);
     __threadfence();  // release this word's L_E and hard decision
     __syncwarp();
@@ -530,9 +569,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
     if (lane == 0) done = atomicAdd(a.done_words + f, 1);
     done = __shfl_sync(FULL, done, 0);
     if (done != n - 1) continue;
-    frame_after_half<NPL>(code, xcode, a, a.ctrl, a.queue, f, li, half, sc.W(), lane);
+    frame_after_half<NPL, GEN>(code, xcode, a, a.ctrl, a.queue, f, li, half, sc.W(), lane);
   }
-  tally.flush(a, lane);
+  tally_flush(sc.tally(), a.wsum, a.xf_count, lane);
 }
 
 // ---- mixed form: frames of several codes (uneven n) in one launch ----
@@ -545,10 +584,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
 // group's lanes-per-bit count NPL.
 template <class SYN, int NPL>
 __device__ __forceinline__ int mixed_word(const MixGroup &G, unsigned char *smem, int warp, int wstride, int dpbytes,
-                                          int64_t f, int w, int half, int lane, WarpTally &tally) {
+                                          int64_t f, int w, int half, int lane) {
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, wstride, dpbytes);
-  const int q = product_word<NPL, SYN, true>(G.code, G.P, G.a, sc, f, w, half, lane, tally);
+  const int q = product_word<NPL, SYN, true, false>(G.code, G.P, G.a, sc, f, w, half, lane);
   return q;
 }
 
@@ -558,7 +597,7 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   // the group table, copied into shared memory after the warps' areas, the
   // remaining-mass area and its lock
-  MixGroup *tab = reinterpret_cast<MixGroup *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16);
+  MixGroup *tab = reinterpret_cast<MixGroup *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + TAIL_BYTES);
   {
     const int words = m.ngroups * (int)(sizeof(MixGroup) / 4);
     const int *src = reinterpret_cast<const int *>(m.groups);
@@ -568,7 +607,8 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
   init_block_lock(smem, m.wstride, m.dpbytes);
   unsigned char *wsm = smem + warp * m.wstride;
   const int64_t nslots = m.total * (int64_t)m.max_half;
-  WarpTally tally;
+  unsigned long long *tslot = reinterpret_cast<unsigned long long *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16) + 2 * warp;
+  tally_clear(tslot, lane);
   for (;;) {
     int slot, w, f1;
     if (!sched_take(m.ctrl, m.queue, nslots, m.total, m.slot_n, m.max_spin, lane, &slot, &w, &f1)) break;
@@ -587,11 +627,11 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
     const int npl = G.npl;
     int q;
     if (npl == 1)
-      q = mixed_word<SYN, 1>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane, tally);
+      q = mixed_word<SYN, 1>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane);
     else if (npl == 2)
-      q = mixed_word<SYN, 2>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane, tally);
+      q = mixed_word<SYN, 2>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane);
     else
-      q = mixed_word<SYN, 4>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane, tally);
+      q = mixed_word<SYN, 4>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane);
     if (lane == 0 && q < 0) atomicExch(G.a.bad + f, 1);
     __threadfence();  // release this word's L_E and hard decision
     __syncwarp();
@@ -601,19 +641,16 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
     if (done != G.code.n - 1) continue;
     // the check uses this warp's word area as laid out for the group's NPL
     if (npl == 1)
-      frame_after_half<1>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
+      frame_after_half<1, false>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
                           reinterpret_cast<uint64_t *>(wsm + Layout<1, SYN>::o_w), lane);
     else if (npl == 2)
-      frame_after_half<2>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
+      frame_after_half<2, false>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
                           reinterpret_cast<uint64_t *>(wsm + Layout<2, SYN>::o_w), lane);
     else
-      frame_after_half<4>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
+      frame_after_half<4, false>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
                           reinterpret_cast<uint64_t *>(wsm + Layout<4, SYN>::o_w), lane);
   }
-  if (lane == 0) {
-    if (m.wsum && tally.wsum) atomicAdd(m.wsum, tally.wsum);
-    if (m.xf_count && tally.xf) atomicAdd(m.xf_count, tally.xf);
-  }
+  tally_flush(tslot, m.wsum, m.xf_count, lane);
 }
 
 // List and counters of the mixed form: every listed frame queued for its
@@ -740,19 +777,19 @@ cudaError_t launch_trace(const DevCode &code, const float *lam, int max_q, uint6
   return cudaGetLastError();
 }
 
-template <int NPL, class SYN>
+template <int NPL, class SYN, bool GEN>
 cudaError_t launch_product_half(const DevCode &rowc, const DevCode &colc, const SisoParams &P, const ProductArgs &a,
                                 int half, cudaStream_t s) {
   const int smem = block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
   const int64_t items = a.n_frames * ((half & 1) ? a.nc : a.nr);
   const int minb = rowc.minb;
   if (half & 1) {
-    auto kern = minb == 8 ? k_product_half<NPL, SYN, true, 8> : k_product_half<NPL, SYN, true, 6>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, true, 8, GEN> : k_product_half<NPL, SYN, true, 6, GEN>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
   } else {
-    auto kern = minb == 8 ? k_product_half<NPL, SYN, false, 8> : k_product_half<NPL, SYN, false, 6>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, false, 8, GEN> : k_product_half<NPL, SYN, false, 6, GEN>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
@@ -778,7 +815,7 @@ cudaError_t launch_product_init(const DevCode &code, const ProductArgs &a, cudaS
   return e;
 }
 
-template <int NPL, class SYN>
+template <int NPL, class SYN, bool GEN>
 cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, const SisoParams &P,
                                       const ProductArgs &a, cudaStream_t s) {
   if (a.n_frames <= 0) return cudaSuccess;
@@ -786,7 +823,7 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int smem = block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
-  auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8> : k_product_persistent<NPL, SYN, 6>;
+  auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8, GEN> : k_product_persistent<NPL, SYN, 6, GEN>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
@@ -810,7 +847,7 @@ cudaError_t launch_product_mixed(const MixArgs &m, const MixGroup *host_groups, 
       m, epoch_halves > 0 ? epoch_halves : m.max_half);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int smem = WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16 + m.ngroups * (int)sizeof(MixGroup);
+  const int smem = WARPS_PER_BLOCK * m.wstride + m.dpbytes + TAIL_BYTES + m.ngroups * (int)sizeof(MixGroup);
   auto kern = k_product_mixed<SYN>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
@@ -830,12 +867,22 @@ cudaError_t launch_product_mixed(const MixArgs &m, const MixGroup *host_groups, 
                                                cudaStream_t);                                                    \
   template cudaError_t launch_trace<NPL, SYN>(const DevCode &, const float *, int, uint64_t *, int32_t *,        \
                                               int32_t *, cudaStream_t);                                          \
-  template cudaError_t launch_product_half<NPL, SYN>(const DevCode &, const DevCode &, const SisoParams &,       \
-                                                     const ProductArgs &, int, cudaStream_t);                    \
+  template cudaError_t launch_product_half<NPL, SYN, false>(const DevCode &, const DevCode &, const SisoParams &, \
+                                                            const ProductArgs &, int, cudaStream_t);             \
   template cudaError_t launch_product_check<NPL, SYN>(const DevCode &, const DevCode &, const ProductArgs &, int, \
                                                       cudaStream_t);                                             \
   template cudaError_t launch_product_init<NPL, SYN>(const DevCode &, const ProductArgs &, cudaStream_t);           \
-  template cudaError_t launch_product_persistent<NPL, SYN>(const DevCode &, const DevCode &, const SisoParams &,  \
-                                                           const ProductArgs &, cudaStream_t);
+  template cudaError_t launch_product_persistent<NPL, SYN, false>(const DevCode &, const DevCode &,              \
+                                                                  const SisoParams &, const ProductArgs &,       \
+                                                                  cudaStream_t);
+
+// Launchers of the general geometry (two codes, or wrapped diagonals), in
+// translation units of their own so that they compile in parallel.
+#define SG_INSTANTIATE_GEN(NPL, SYN)                                                                             \
+  template cudaError_t launch_product_half<NPL, SYN, true>(const DevCode &, const DevCode &, const SisoParams &,  \
+                                                           const ProductArgs &, int, cudaStream_t);              \
+  template cudaError_t launch_product_persistent<NPL, SYN, true>(const DevCode &, const DevCode &,               \
+                                                                 const SisoParams &, const ProductArgs &,        \
+                                                                 cudaStream_t);
 
 }  // namespace sg

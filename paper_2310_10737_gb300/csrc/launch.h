@@ -106,7 +106,9 @@ cudaError_t launch_product_init(const DevCode &code, const ProductArgs &a, cudaS
 
 // Product launchers take the row code (words of a row half) and the column
 // code (words of a column half); a square product code passes one code twice.
-template <int NPL, class SYN>
+// GEN = false is the square product code of one code (rowc == colc,
+// nr == nc == n, no diagonals); GEN = true any other geometry.
+template <int NPL, class SYN, bool GEN>
 cudaError_t launch_product_half(const DevCode &rowc, const DevCode &colc, const SisoParams &P, const ProductArgs &a,
                                 int half, cudaStream_t s);
 
@@ -114,7 +116,7 @@ template <int NPL, class SYN>
 cudaError_t launch_product_check(const DevCode &rowc, const DevCode &colc, const ProductArgs &a, int half,
                                  cudaStream_t s);
 
-template <int NPL, class SYN>
+template <int NPL, class SYN, bool GEN>
 cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, const SisoParams &P,
                                       const ProductArgs &a, cudaStream_t s);
 

@@ -193,7 +193,12 @@ struct RankRec {
 
 // Shared memory of a block: one area per warp (below), then one
 // remaining-mass area for the whole block (the cost DP, needed by about 0.2%
-// of component decodings) guarded by a lock word.
+// of component decodings), then a tail: the area's lock word (16 bytes) and
+// one 16-byte tally slot per warp (summed pattern weights, extended-range
+// words), flushed to global counters when the warp exits.
+// lock word + one tally slot per warp, after the block's remaining-mass area
+constexpr int TAIL_BYTES = 16 + 16 * WARPS_PER_BLOCK;
+
 template <int NPL, class SYN>
 struct Layout {
   static constexpr int NT = 32 * NPL;
@@ -206,11 +211,12 @@ struct Layout {
   static constexpr int o_wl = o_lp + 4 * LMAX;                        // float[LMAX] APP of each listed word
   static constexpr int o_perm = o_wl + 4 * LMAX;                      // u8[NT] rank -> bit
   static constexpr int o_w = align16(o_perm + NT);                    // u64[NT][NM] words of a frame (check)
-  static constexpr int warp_bytes = align16(o_w + 8 * NT * NM);
+  static constexpr int o_lam = align16(o_w + 8 * NT * NM);            // float[NT] the word's lambda, by bit
+  static constexpr int warp_bytes = align16(o_lam + 4 * NT);
   // block area (sized for the 8-byte XF policy): sfac[NT+1], fu[NT+1], fb[NT+1], ek[J] (float), he[J], ho[J]
   static __host__ __device__ int dp_bytes(int jm) { return align16(24 * (NT + 1) + 20 * jm + 32); }
-  // a block of WARPS_PER_BLOCK warps: their areas, the remaining-mass area and its lock word
-  static __host__ __device__ int block_bytes(int jm) { return WARPS_PER_BLOCK * warp_bytes + dp_bytes(jm) + 16; }
+  // a block of WARPS_PER_BLOCK warps: their areas, the remaining-mass area and the tail
+  static __host__ __device__ int block_bytes(int jm) { return WARPS_PER_BLOCK * warp_bytes + dp_bytes(jm) + TAIL_BYTES; }
 };
 
 // A warp's view of the block's shared memory: its own area and the block's
@@ -235,8 +241,16 @@ struct Scratch {
   __device__ float *wl() const { return reinterpret_cast<float *>(base + LY::o_wl); }
   __device__ uint8_t *perm() const { return base + LY::o_perm; }
   __device__ uint64_t *W() const { return reinterpret_cast<uint64_t *>(base + LY::o_w); }
+  // lambda by bit, kept here during the search and read back (volatile) for
+  // the soft output, so that it holds no registers while the search runs
+  __device__ float *lamv() const { return reinterpret_cast<float *>(base + LY::o_lam); }
+  __device__ float lam_at(int i) const { return *reinterpret_cast<const volatile float *>(base + LY::o_lam + 4 * i); }
   __device__ unsigned char *tail() const { return dp; }
   __device__ int *lock() const { return reinterpret_cast<int *>(dp + dpbytes); }
+  // this warp's tally slot: [0] summed pattern weights, [1] extended-range words
+  __device__ unsigned long long *tally() const {
+    return reinterpret_cast<unsigned long long *>(dp + dpbytes + 16) + 2 * (threadIdx.x >> 5);
+  }
 };
 
 // The block's remaining-mass area is taken by one warp at a time.  Its holder
@@ -999,6 +1013,8 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
 #ifdef SG_PHASE_PROFILE
   const long long t0 = clock64();
 #endif
+#pragma unroll
+  for (int k = 0; k < NPL; k++) sc.lamv()[lane + 32 * k] = lam[k];  // each lane reads back its own
   WordHead<NPL, SYN> h;
   if (!siso_prologue<NPL, SYN>(code, sc, lam, lane, h)) {
 #pragma unroll
@@ -1096,7 +1112,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   res.nhit = nhit;
   if (nhit == 0) {
 #pragma unroll
-    for (int k = 0; k < NPL; k++) lapp[k] = lam[k];
+    for (int k = 0; k < NPL; k++) lapp[k] = sc.lam_at(lane + 32 * k);
     res.pmiss = 1.f;
     res.logD = M;
   } else {
@@ -1115,7 +1131,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
       const int i = lane + 32 * k;
-      const float x = lam[k];
+      const float x = sc.lam_at(i);
       // sigma(x) and sigma(-x) without cancellation
       const float ex = expf(-fabsf(x));
       const float sp = __frcp_rn(1.f + ex), sn = ex * sp;  // sigma(|x|), sigma(-|x|)

@@ -17,7 +17,7 @@ import os
 import numpy as np
 import pytest
 
-from workloads import awgn_frames, ebch
+from workloads import awgn_frames, ebch, shorten
 
 pytestmark = pytest.mark.gpu
 
@@ -336,6 +336,32 @@ def test_non_square_product_codes(env, oracle_lib, row, col, ebn0, hi, F):
         assert valid == (outs[1]["status"][f] == 0)
     cr.close()
     ccol.close()
+
+
+@pytest.mark.parametrize("kind", ["shortened", "punctured"])
+def test_rate_adapted_product_codes(env, oracle_lib, kind):
+    """Shortened components ((60,53) from eBCH(64,57)) and punctured frames
+    (3% of the coded bits erased, L_Ch = 0) against the oracle."""
+    F = 90
+    if kind == "shortened":
+        code, mask, ebn0 = shorten(ebch("ebch_64_57"), 4), None, 3.0
+    else:
+        code, ebn0 = ebch("ebch_64_57"), 3.25
+        mask = np.random.default_rng(31).random((64, 64)) < 0.03
+    snr = np.where(np.arange(F) % 3 == 2, 6.0 if mask is None else 7.0, ebn0)
+    U, X, lch = awgn_frames(code, F, snr, seed=1400 + F, punctured=mask)
+    g = _decode(env, code, lch, L=4, query_cap=10**4, alpha=0.5, max_iter=20)
+    r = oracle_lib.product_batch(oracle_lib.OracleCode(code), lch, L=4, cap=10**4, alpha=0.5, max_iter=20)
+    first = r["half_iters"] == 1
+    assert first.sum() >= 5
+    np.testing.assert_array_equal(g["half_iters"][first], 1)
+    np.testing.assert_array_equal(g["queries"][first], r["queries"][first])
+    np.testing.assert_array_equal(g["frames"][first], r["bits"][first])
+    assert (g["frames"] == r["bits"]).reshape(F, -1).all(axis=1).mean() >= 0.97
+    for f in range(F):
+        B = g["frames"][f]
+        assert (not code.syndrome(B).any() and not code.syndrome(B.T).any()) == (g["status"][f] == 0)
+    assert ((g["frames"] != X).reshape(F, -1).any(axis=1)).mean() < 0.2
 
 
 def test_product_codes_of_different_kernel_classes_are_refused(env):
