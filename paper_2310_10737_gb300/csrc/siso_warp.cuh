@@ -726,6 +726,38 @@ __device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, in
   return {__shfl_sync(FULL, E.h, 0), __shfl_sync(FULL, E.l, 0)};
 }
 
+// The unqueried patterns summed directly: the cost DP of remaining_scaled
+// under the block's lock (out of line: about 0.2% of product-decoding words
+// get here, and both inlined call sites of remaining_log2 stay short).
+template <int NPL, class SYN>
+__device__ __noinline__ float remaining_log2_dp(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs,
+                                                int n, int c, int cls, int lane, int *used_xf) {
+#ifdef SG_PHASE_PROFILE
+  if (lane == 0) SG_PROF(6, 1);
+#endif
+  const int Cs = __ldg(O.cost + tb + qs);
+  const int R0 = min(max(Cs - c, 0), n);
+  float g = CUDART_INF_F;
+  for (int e = lane; e < R0; e += 32) g = fminf(g, sc.l2()[e] / (float)(e + 1 + c));
+  g = __shfl_sync(FULL, warp_min_f(g), 0);
+  if (!(g < CUDART_INF_F)) g = 0.f;
+  const bool held = dp_lock(sc.lock(), lane);
+  float out;
+  const float tot = __shfl_sync(FULL, remaining_scaled<FOps, NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, g, lane), 0);
+  if (tot >= 0x1p-60f && tot < CUDART_INF_F) {
+    out = log2f(tot) - g * (float)Cs;
+  } else {
+    if (used_xf) *used_xf |= 1;
+#ifdef SG_PHASE_PROFILE
+    if (lane == 0) SG_PROF(8, 1);
+#endif
+    out = remaining_log2_xf<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, lane);
+  }
+  dp_unlock(sc.lock(), held, lane);
+  if (!held && used_xf) *used_xf |= 2;
+  return out;
+}
+
 // log2 of the remaining (unqueried) mass relative to p(0^n|r); warp-uniform.
 // *used_xf (if given) gets bit 0 when the extended-range sum was needed and
 // bit 1 when the block's remaining-mass area could not be locked.
@@ -781,30 +813,7 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
     if (!in_range && lane == 0) SG_PROF(15, 1);
 #endif
   }
-#ifdef SG_PHASE_PROFILE
-  if (lane == 0) SG_PROF(6, 1);
-#endif
-  const int Cs = __ldg(O.cost + tb + qs);
-  const int R0 = min(max(Cs - c, 0), n);
-  float g = CUDART_INF_F;
-  for (int e = lane; e < R0; e += 32) g = fminf(g, sc.l2()[e] / (float)(e + 1 + c));
-  g = __shfl_sync(FULL, warp_min_f(g), 0);
-  if (!(g < CUDART_INF_F)) g = 0.f;
-  const bool held = dp_lock(sc.lock(), lane);
-  float out;
-  const float tot = __shfl_sync(FULL, remaining_scaled<FOps, NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, g, lane), 0);
-  if (tot >= 0x1p-60f && tot < CUDART_INF_F) {
-    out = log2f(tot) - g * (float)Cs;
-  } else {
-    if (used_xf) *used_xf |= 1;
-#ifdef SG_PHASE_PROFILE
-    if (lane == 0) SG_PROF(8, 1);
-#endif
-    out = remaining_log2_xf<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, Cs, lane);
-  }
-  dp_unlock(sc.lock(), held, lane);
-  if (!held && used_xf) *used_xf |= 2;
-  return out;
+  return remaining_log2_dp<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, lane, used_xf);
 }
 
 // numerically safe log(exp(a) + exp(b)) (natural log, -inf aware)
@@ -1050,6 +1059,8 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
 #endif
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
     if (lane < lim) e = __ldg(O.ent + tb + q + lane);
+    // the next chunk's entries into L1 while this one is tested (within the stored entries)
+    if (q + 32 + lane < qlim) asm volatile("prefetch.global.L1 [%0];" ::"l"(O.ent + tb + q + 32 + lane));
     const int w = e.x & 0xff;
     const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
     DF mass;
