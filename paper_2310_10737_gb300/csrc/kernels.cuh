@@ -158,6 +158,7 @@ struct WordCtx {
   int64_t f, li;
   int32_t wd, half;
 };
+static_assert(sizeof(WordCtx) <= 32, "the word's lambda follows the context in the frame-check area");
 
 // One component word of frame f in half `half` (rows when odd): lambda =
 // L_Ch + fl32(alpha L_E) (L_A = 0 in the first half), SOGRAND, then L_E and

@@ -211,8 +211,13 @@ struct Layout {
   static constexpr int o_wl = o_lp + 4 * LMAX;                        // float[LMAX] APP of each listed word
   static constexpr int o_perm = o_wl + 4 * LMAX;                      // u8[NT] rank -> bit
   static constexpr int o_w = align16(o_perm + NT);                    // u64[NT][NM] words of a frame (check)
-  static constexpr int o_lam = align16(o_w + 8 * NT * NM);            // float[NT] the word's lambda, by bit
-  static constexpr int warp_bytes = align16(o_lam + 4 * NT);
+  // During a word the frame-check area is free: its first 32 bytes hold the
+  // word's context (product kernels) and then float[NT] the word's lambda.
+  // (A separate area would cost 1 KB per block, which moved the shared-memory
+  // carveout of the 8-block schedule up a step and shrank L1 by a quarter.)
+  static constexpr int o_lam = o_w + 32;
+  static_assert(32 + 4 * NT <= 8 * NT * NM, "lambda fits in the frame-check area");
+  static constexpr int warp_bytes = align16(o_w + 8 * NT * NM);
   // block area (sized for the 8-byte XF policy): sfac[NT+1], fu[NT+1], fb[NT+1], ek[J] (float), he[J], ho[J]
   static __host__ __device__ int dp_bytes(int jm) { return align16(24 * (NT + 1) + 20 * jm + 32); }
   // a block of WARPS_PER_BLOCK warps: their areas, the remaining-mass area and the tail
