@@ -46,10 +46,23 @@ METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 # digest is recorded with it: `traffic` is null once they change.
 TRAFFIC = {"csrc_digest": "b2cca6381f0c02208748d45f351ba0998608db6b34ea4c02998965556c80d5a6",
            "bytes_per_frame": 307314.6,
-           "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md"}
+           "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md",
+           # pipe activity of the same capture (percent of peak sustained over active cycles)
+           "ncu": {"issue_active_pct": 49.3, "alu_pipe_pct": 34.1, "fma_pipe_pct": 16.2,
+                   "tensor_pipe_pct": 0.0, "dram_throughput_pct": 1.1}}
 
 
 KERNEL_SOURCES = ("kernels.cuh", "launch.h", "sg_common.h", "siso_warp.cuh")  # what k_product_persistent compiles from
+
+
+def measured_hbm_gbs():
+    """The machine's measured copy bandwidth (GB/s), or None without the peaks file."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            v = json.load(fh).get("hbm_gbs")
+        return float(v) if v is not None else None
+    except (OSError, ValueError, TypeError):
+        return None
 
 
 def csrc_digest():
@@ -431,8 +444,16 @@ def main():
     peak = int_peak / 1e12
     achieved = ops / (t_half / 1000) / 1e12 if t_half > 0 else 0.0
     traffic = None
-    if main_persistent and TRAFFIC["csrc_digest"] == csrc_digest():
+    same_kernel = main_persistent and TRAFFIC["csrc_digest"] == csrc_digest()
+    if same_kernel:
         traffic = TRAFFIC["bytes_per_frame"] * F
+    # HBM side: the LLRs in and decided bits out (algorithmic) and, from the capture, DRAM bytes
+    t_launch_s = t_half / 1000 / max(half_launches, 1)
+    llr_bytes = F * (4 * n * n + n * n // 8)
+    hbm = {"algorithmic_bytes_per_launch": llr_bytes,
+           "algorithmic_gbs": llr_bytes / t_launch_s / 1e9 if t_launch_s > 0 else None,
+           "dram_gbs": traffic / t_launch_s / 1e9 if traffic is not None and t_launch_s > 0 else None,
+           "peak_gbs": measured_hbm_gbs()}
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tops/s",
                 "frac": achieved / peak if peak else None, "traffic": traffic,
                 "traffic_source": TRAFFIC["source"] if traffic is not None else None,
@@ -443,7 +464,9 @@ def main():
                 "kernel_share": t_half / (t_half + t_check) if t_half + t_check else None,
                 "peak_def": f"measured: 32-bit LOP3 + IADD lane-ops/s at full occupancy (sogrand_int_peak, "
                             f"{int_ms:.1f} ms kernel); nominal 152 SMs x 128 lanes x {sm_max:.0f} MHz = "
-                            f"{nominal:.2f} Tops/s"}
+                            f"{nominal:.2f} Tops/s",
+                "hbm": hbm,
+                "ncu": dict(TRAFFIC["ncu"], source=TRAFFIC["source"]) if same_kernel else None}
 
     # end to end through the C ABI on host buffers (copies inside the timed region)
     hout = dict(bits=torch.empty((F, n * n // 8), dtype=torch.uint8, pin_memory=True),
