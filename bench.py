@@ -44,7 +44,7 @@ METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 # capture of a 10,000-frame decode of this workload (traffic grows with the
 # frame count at a fixed Eb/N0 mix), valid only for the kernel sources whose
 # digest is recorded with it: `traffic` is null once they change.
-TRAFFIC = {"csrc_digest": "b2cca6381f0c02208748d45f351ba0998608db6b34ea4c02998965556c80d5a6",
+TRAFFIC = {"csrc_digest": "a04d3bec1fc48855e2549330b9bf212b6acdba1041d19b843298ac4f30b38f8e",
            "bytes_per_frame": 307314.6,
            "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md",
            # pipe activity of the same capture (percent of peak sustained over active cycles)

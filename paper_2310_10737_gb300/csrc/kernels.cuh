@@ -151,9 +151,10 @@ __device__ __forceinline__ void tally_flush(const unsigned long long *slot, unsi
   if (xf_count && slot[1]) atomicAdd(xf_count, (int32_t)slot[1]);
 }
 
-// The words' context (frame, word, half, list index) is kept in the frame
-// check area sc.W(), which nothing uses during a word, and read back after
-// the search: the registers that held it are free while the search runs.
+// A word's context (frame, word, half, list index) is kept at the start of
+// the frame-check area sc.W(), which nothing else uses during a word (the
+// word's lambda follows it), and read back after the search: the registers
+// that held it are free while the search runs.
 struct WordCtx {
   int64_t f, li;
   int32_t wd, half;
