@@ -427,8 +427,11 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode rowc, const
 // ---- persistent forms: one launch decodes the whole batch ----
 
 // Draw a word ticket and wait until its slot of the frame-half list is
-// filled.  Returns 1 with *f1 = frame + 1 (list entry), or 0 when the launch
-// is over (every frame finished or parked, or the error flag is set).  The
+// filled.  A filled slot holds +(e + 1) for an odd half of list entry e and
+// -(e + 1) for an even one: the slot itself says which half it is, so a
+// ticket that the half skips (codes of different lengths) is recognised even
+// after the frame has moved on to its next half.  Returns 1 with *f1 = the
+// signed slot value, or 0 when the launch is over (every frame finished or parked, or the error flag is set).  The
 // wait backs off exponentially and gives up after max_spin microseconds of
 // sleep, setting the error flag.  All reads of shared state are made by lane 0
 // and broadcast, so the whole warp takes the same branch.
@@ -514,14 +517,16 @@ __device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCod
     a.done_words[f] = 0;
     __threadfence();
     const int t = atomicAdd(ctrl + 0, 1);  // < nslots: every frame appends at most max_half - 1 times
-    atomicExch(queue_w + t, (int)(gf + 1));
+    const int e = (int)(gf + 1);
+    atomicExch(queue_w + t, ((half + 1) & 1) ? e : -e);  // the sign gives the half's parity
   }
   __syncwarp();
 }
 
-// Frame-halves are appended to a list (a.queue[s] = frame + 1 once slot s is
-// filled); the first F slots hold every frame's first half.  Warps draw
-// global word tickets T: slot T / n, word T mod n, one atomic per word.  The
+// Frame-halves are appended to a list (a.queue[s] = +-(frame + 1) once slot s
+// is filled, negative for an even half); the first F slots hold every
+// frame's current half.  Warps draw global word tickets T: slot T / slot_n,
+// word T mod slot_n, one atomic per word.  The
 // warp that completes a frame's last word of a half runs the frame check and
 // either finishes the frame or appends it for its next half.  A warp whose
 // slot is not filled yet waits with exponential back-off; all waits are
@@ -547,15 +552,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
   for (;;) {
     int slot, w, f1;
     if (!sched_take(a.ctrl, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1)) break;
-    int64_t li = (int64_t)f1 - 1;  // list index
-    int64_t f = a.frame_list ? (int64_t)a.frame_list[li] : li;
-    int half = 0;
-    if (lane == 0) half = __ldcg(a.half_cur + f);
-    half = __shfl_sync(FULL, half, 0);
-    const bool rows = (half & 1) != 0;
+    const bool rows = f1 > 0;                      // the slot's half is odd: a row half
+    int64_t li = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // list index
     const DevCode &code = GEN ? (rows ? rowc : colc) : rowc, &xcode = GEN ? (rows ? colc : rowc) : rowc;
     const int n = xcode.n;  // words in this half
-    if (GEN && w >= n) continue;  // a ticket past this half's words (codes of different lengths)
+    // a ticket past this half's words (codes of different lengths); decided
+    // from the slot, since the frame may already be in its next half
+    if (GEN && w >= n) continue;
+    int64_t f = a.frame_list ? (int64_t)a.frame_list[li] : li;
+    int half = 0;  // the slot's half: the frame cannot leave it before this word is done
+    if (lane == 0) half = __ldcg(a.half_cur + f);
+    half = __shfl_sync(FULL, half, 0);
     if (lane == 0) reinterpret_cast<WordCtx *>(sc.W())->li = li;
     const int q = product_word<NPL, SYN, true, GEN>(code, P, a, sc, f, w, half, lane);
     {
@@ -614,7 +621,7 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
   for (;;) {
     int slot, w, f1;
     if (!sched_take(m.ctrl, m.queue, nslots, m.total, m.slot_n, m.max_spin, lane, &slot, &w, &f1)) break;
-    const int64_t gf = (int64_t)f1 - 1;
+    const int64_t gf = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // the sign (the half's parity) is not needed here
     int g = 0;
     if (lane == 0)
       while (g + 1 < m.ngroups && m.groups[g + 1].first <= gf) g++;
@@ -662,7 +669,7 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
 static __global__ void k_mixed_init(const MixArgs m, int epoch_halves) {
   const int64_t slots = m.total * (int64_t)m.max_half;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
-    m.queue[i] = i < m.total ? (int32_t)(i + 1) : 0;
+    if (i >= m.total) m.queue[i] = 0;
     if (i < m.total) {
       int g = 0;
       while (g + 1 < m.ngroups && m.groups[g + 1].first <= i) g++;
@@ -678,6 +685,7 @@ static __global__ void k_mixed_init(const MixArgs m, int epoch_halves) {
       G.a.done_words[f] = 0;
       G.a.hmax[f] = 0;
       if (G.a.half_stop) G.a.half_stop[f] = G.a.half_cur[f] + epoch_halves - 1;
+      m.queue[i] = (G.a.half_cur[f] & 1) ? (int32_t)(i + 1) : -(int32_t)(i + 1);
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -694,7 +702,7 @@ static __global__ void k_persistent_init(const ProductArgs a) {
   const int64_t slots = F * (int64_t)a.max_half;
   int32_t *queue = a.queue;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
-    queue[i] = i < F ? (int32_t)(i + 1) : 0;
+    if (i >= F) queue[i] = 0;
     if (i < F) {
       int64_t f = i;
       bool fresh = true;
@@ -714,6 +722,7 @@ static __global__ void k_persistent_init(const ProductArgs a) {
       a.done_words[f] = 0;
       a.hmax[f] = 0;
       if (a.half_stop) a.half_stop[f] = a.half_cur[f] + a.epoch_halves - 1;
+      queue[i] = (a.half_cur[f] & 1) ? (int32_t)(i + 1) : -(int32_t)(i + 1);  // signed by the half's parity
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {

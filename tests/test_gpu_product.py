@@ -364,6 +364,36 @@ def test_rate_adapted_product_codes(env, oracle_lib, kind):
     assert ((g["frames"] != X).reshape(F, -1).any(axis=1)).mean() < 0.2
 
 
+def test_non_square_batched_form_is_repeatable(env):
+    """Codes of different lengths leave tickets of a half unused; such a
+    ticket must be recognised from its slot even when the frame has already
+    moved on to its next half (with the next half's word count), or a word of
+    that half is decoded twice.  Repeated batched decodes (device and host
+    entry points) must equal the plain form in every output."""
+    torch, sg = env
+    rc, cc = ebch("ebch_32_26"), ebch("ebch_16_11")
+    F = 600
+    snr = np.where(np.arange(F) % 3 == 2, 5.0, 3.0)
+    U, X, lch = awgn_frames(rc, F, snr, seed=1777, col_code=cc)
+    cr, ccol = sg.Code.from_linear_code(rc), sg.Code.from_linear_code(cc)
+    d = torch.from_numpy(lch).cuda()
+    kw = dict(L=4, query_cap=10**4, alpha=0.5, max_iter=10, col_code=ccol)
+    ref = sg.product_decode(cr, d, persistent=False, **kw)
+    torch.cuda.synchronize()
+    ref = {k: v.cpu().numpy() for k, v in ref.items() if hasattr(v, "cpu")}
+    pin = torch.from_numpy(lch).pin_memory()
+    for rep in range(6):
+        o = sg.product_decode(cr, d, persistent=True, **kw)
+        torch.cuda.synchronize()
+        for key in ("bits", "half_iters", "status", "queries", "par_queries"):
+            np.testing.assert_array_equal(o[key].cpu().numpy(), ref[key], err_msg=f"{key}, run {rep}")
+        h = sg.product_decode_host(cr, pin, **kw)
+        for key in ("bits", "half_iters", "status", "queries"):
+            np.testing.assert_array_equal(h[key], ref[key], err_msg=f"host {key}, run {rep}")
+    cr.close()
+    ccol.close()
+
+
 def test_product_codes_of_different_kernel_classes_are_refused(env):
     torch, sg = env
     cr, ccol = sg.Code.from_linear_code(ebch("ebch_64_57")), sg.Code.from_linear_code(ebch("ebch_32_26"))
