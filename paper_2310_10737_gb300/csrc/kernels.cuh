@@ -69,7 +69,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const 
     float lapp[NPL];
     WordResult res;
     int used_xf = 0;
-    siso_word<NPL, SYN>(code, P, sc, lam, lane, lapp, res, &used_xf);
+    siso_word<NPL, SYN, MINB == 8>(code, P, sc, lam, lane, lapp, res, &used_xf);
     const bool empty = res.nhit == 0;
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
@@ -169,7 +169,7 @@ static_assert(sizeof(WordCtx) <= 32, "the word's lambda follows the context in t
 // and the second set of words may be wrapped diagonals (a.diag); otherwise
 // it is a square code.n x code.n frame with columns as the second set.
 // Returns the word's query count (-1: non-finite input).
-template <int NPL, class SYN, bool COHERENT, bool GEN>
+template <int NPL, class SYN, bool COHERENT, bool GEN, bool DP_CALL>
 __device__ __forceinline__ int product_word(const DevCode &code, const SisoParams &P, const ProductArgs &a,
                                             const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
@@ -202,7 +202,7 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     ctx->half = half;
   }
   __syncwarp();
-  siso_word<NPL, SYN>(code, P, sc, lam, lane, lapp, res, &used_xf);
+  siso_word<NPL, SYN, DP_CALL>(code, P, sc, lam, lane, lapp, res, &used_xf);
   bool rows2;
   {
     const volatile WordCtx *vc = ctx;
@@ -382,7 +382,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode rowc, 
     const int32_t fs = __ldg(a.fstate + f);
     if (fs != F_RUN && fs != F_BAD_PENDING) continue;  // finished frames only: a flag raised during
                                                         // this half must not change which words run
-    const int q = product_word<NPL, SYN, false, GEN>(code, P, a, sc, f, wd, half, lane);
+    const int q = product_word<NPL, SYN, false, GEN, MINB == 8>(code, P, a, sc, f, wd, half, lane);
     if (lane == 0 && q < 0) atomicExch(a.fstate + f, (int32_t)F_BAD_PENDING);
   }
   tally_flush(sc.tally(), a.wsum, a.xf_count, lane);
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
     if (lane == 0) reinterpret_cast<WordCtx *>(sc.W())->li = li;
-    const int q = product_word<NPL, SYN, true, GEN>(code, P, a, sc, f, w, half, lane);
+    const int q = product_word<NPL, SYN, true, GEN, MINB == 8>(code, P, a, sc, f, w, half, lane);
     {
       const volatile WordCtx *vc = reinterpret_cast<const volatile WordCtx *>(sc.W());
       f = vc->f;
@@ -596,7 +596,7 @@ __device__ __forceinline__ int mixed_word(const MixGroup &G, unsigned char *smem
                                           int64_t f, int w, int half, int lane) {
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, wstride, dpbytes);
-  const int q = product_word<NPL, SYN, true, false>(G.code, G.P, G.a, sc, f, w, half, lane);
+  const int q = product_word<NPL, SYN, true, false, false>(G.code, G.P, G.a, sc, f, w, half, lane);
   return q;
 }
 
