@@ -47,3 +47,21 @@ def test_oracle_gldpc_decoder(oracle_lib):
     # not the product code: the same channel output decodes differently as a product frame
     rp = oracle_lib.product_batch(oc, L[:5], alpha=0.6, max_iter=20)
     assert (rp["half_iters"] != r["half_iters"][:5]).any() or (rp["bits"] != r["bits"][:5]).any()
+
+
+def test_oracle_gldpc_fixes_weak_single_errors_in_the_first_half(oracle_lib):
+    """One weak wrong-sign bit in every row of a clean frame: the row half
+    corrects each row (its single flip is the first query of the right
+    parity), so every row and wrapped diagonal is a codeword after one half."""
+    c = ebch("ebch_32_26")
+    g = QCGLDPC(c)
+    oc = oracle_lib.OracleCode(c)
+    U, X, L = gldpc_frames(g, 4, 3.0, seed=21)
+    rng = np.random.default_rng(22)
+    clean = (8.0 * (1.0 - 2.0 * X)).astype(np.float32)
+    cols = rng.integers(0, 32, size=(4, 32))
+    for f in range(4):
+        clean[f, np.arange(32), cols[f]] *= -0.0625  # wrong sign, |LLR| = 0.5
+    r = oracle_lib.gldpc_batch(oc, clean, alpha=0.6, max_iter=4)
+    assert (r["half_iters"] == 1).all() and (r["status"] == 0).all()
+    assert (r["bits"] == X).all()
