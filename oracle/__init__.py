@@ -8,8 +8,11 @@ It shares no code with the CUDA path.  Every function is documented in
 Parity pins (see tests/test_oracle_*.py): exhaustive 2^n enumeration on tiny
 codes, partition counts, pattern distinctness and coverage, codeword
 membership, the complement identity of the remaining mass, the closed form of
-the L=1 corollary and the APP normalisation.
+the L=1 corollary, the APP normalisation and, for product decoding, the
+extrinsic exchange between half iterations (brute-force turbo chain with
+exhaustive lists).
 """
 from .oracle import (  # noqa: F401
-    OracleCode, build, gldpc, gldpc_batch, lib, one_line_c, product, product_batch, siso, siso_batch, trace,
+    OracleCode, build, gldpc, gldpc_batch, lib, one_line_c, product, product_batch, product_trace, siso, siso_batch,
+    trace,
 )

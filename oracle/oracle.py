@@ -54,6 +54,8 @@ def lib():
                                           C.c_double, C.c_float, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
                                           C.c_void_p, C.c_void_p]
             L.oracle_product2.restype = C.c_int
+            L.oracle_product_trace.argtypes = L.oracle_product2.argtypes + [C.c_void_p]
+            L.oracle_product_trace.restype = C.c_int
             L.oracle_gldpc.argtypes = L.oracle_product.argtypes
             L.oracle_gldpc.restype = C.c_int
             _lib = L
@@ -159,6 +161,25 @@ def product(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20
                           _ptr(bits), _ptr(hi), _ptr(st), _ptr(q), _ptr(qp))
     return dict(bits=bits.reshape(nc, nr), half_iters=int(hi[0]), status=int(st[0]), queries=int(q[0]),
                 par_queries=int(qp[0]))
+
+
+def product_trace(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20,
+                  col: OracleCode | None = None) -> dict:
+    """product() of one frame with the L_APP of every half iteration:
+    lapp_trace [2 max_iter, n_col, n_row] (NaN for halves not run)."""
+    col = oc if col is None else col
+    nr, nc = oc.n, col.n
+    lch = np.ascontiguousarray(lch, dtype=np.float32).reshape(nr * nc)
+    bits = np.zeros(nr * nc, np.uint8)
+    hi = np.zeros(1, np.int32)
+    st = np.zeros(1, np.uint8)
+    q = np.zeros(1, np.int64)
+    qp = np.zeros(1, np.int64)
+    tr = np.full((2 * max_iter, nc, nr), np.nan)
+    lib().oracle_product_trace(C.byref(oc._s), C.byref(col._s), _ptr(lch), L, cap, thr, C.c_float(alpha), max_iter,
+                               _ptr(bits), _ptr(hi), _ptr(st), _ptr(q), _ptr(qp), _ptr(tr))
+    return dict(bits=bits.reshape(nc, nr), half_iters=int(hi[0]), status=int(st[0]), queries=int(q[0]),
+                par_queries=int(qp[0]), lapp_trace=tr)
 
 
 def gldpc(oc: OracleCode, lch, L=4, cap=10**4, thr=0.0, alpha=0.5, max_iter=20) -> dict:

@@ -580,7 +580,7 @@ static int frame_valid(const oracle_code *row, const oracle_code *col, int diag,
  */
 static int product_core(const oracle_code *row, const oracle_code *col, int diag, const float *lch, int L,
                         int64_t cap, double thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
-                        uint8_t *status, int64_t *queries, int64_t *par_queries)
+                        uint8_t *status, int64_t *queries, int64_t *par_queries, double *lapp_trace)
 {
     int nr = row->n, nc = col->n;
     size_t nn = (size_t)nr * nc;
@@ -616,6 +616,7 @@ static int product_core(const oracle_code *row, const oracle_code *col, int diag
                 size_t pos = rows ? (size_t)w * nr + i : second_pos(diag, nr, w, i);
                 LE[pos] = (float)lext[i];
                 B[pos] = hd[i];
+                if (lapp_trace) lapp_trace[(size_t)(h - 1) * nn + pos] = lapp[i];
             }
         }
         qpar += qmax;
@@ -642,7 +643,7 @@ int oracle_product2(const oracle_code *row, const oracle_code *col, const float 
                     int64_t *queries, int64_t *par_queries)
 {
     return product_core(row, col, 0, lch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
-                        par_queries);
+                        par_queries, NULL);
 }
 
 /* QC-GLDPC of a component code (Sec. VI): rows and wrapped diagonals of an
@@ -653,7 +654,7 @@ int oracle_gldpc(const oracle_code *code, const float *lch, int L, int64_t cap, 
                  int64_t *par_queries)
 {
     return product_core(code, code, 1, lch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
-                        par_queries);
+                        par_queries, NULL);
 }
 
 /* square product code: the same code on rows and columns */
@@ -663,4 +664,16 @@ int oracle_product(const oracle_code *code, const float *lch, int L, int64_t cap
 {
     return oracle_product2(code, code, lch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
                            par_queries);
+}
+
+/* The product decoder above with the L_APP of every half iteration recorded:
+   lapp_trace [2 * max_iter][n_col * n_row], row-major positions, entry h - 1
+   holding half h's L_APP (halves the frame did not run are left untouched).
+   For pinning the extrinsic exchange between halves. */
+int oracle_product_trace(const oracle_code *row, const oracle_code *col, const float *lch, int L, int64_t cap,
+                         double thr, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters, uint8_t *status,
+                         int64_t *queries, int64_t *par_queries, double *lapp_trace)
+{
+    return product_core(row, col, 0, lch, L, cap, thr, alpha, max_iter, bits, half_iters, status, queries,
+                        par_queries, lapp_trace);
 }
