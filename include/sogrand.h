@@ -81,6 +81,25 @@ int sogrand_code_reserve(sogrand_code *code, int64_t max_query_cap);
 int sogrand_code_info(const sogrand_code *code, int *n, int *k);
 
 /*
+ * Limits of the bounded device-side waits (process-wide; read when a decode
+ * is launched, so set them while no decode is being launched).  The paper has
+ * no counterpart: these bound the GPU decoders' own synchronisation.
+ *   queue_wait_us  microseconds of accumulated back-off that a warp of a
+ *                  batched (persistent) launch waits for work before the
+ *                  launch stops and returns SOGRAND_ETIMEOUT (default
+ *                  2,000,000; 0 gives up at the first wait)
+ *   lock_polls     polls of its block's remaining-mass lock after which a
+ *                  warp gives up on the lock (default 2^22); the batched forms
+ *                  then stop and return SOGRAND_ETIMEOUT
+ *   lock_preheld   1: every block starts with its remaining-mass lock taken,
+ *                  as if a warp held it and never released it (tests of the
+ *                  bound; decoding results are then invalid); 0: normal
+ * A negative value keeps the current setting.  Errors: EINVAL (a value above
+ * 2^31 - 1, lock_preheld > 1).
+ */
+int sogrand_set_wait_limits(int64_t queue_wait_us, int64_t lock_polls, int lock_preheld);
+
+/*
  * SOGRAND soft-input soft-output decoding of n_words independent words
  * (Fig. siso; Sec. IV Corollary; Sec. V-B eq. LLRi).  One warp per word.
  *   llr_ch     device [n_words][n] channel LLRs L_Ch
@@ -175,10 +194,23 @@ typedef struct {
                             and of the frame-check kernels, from CUDA events on
                             `stream` around each launch */
   int32_t *launches;     /* HOST [1]: kernels launched by the call */
+  /* Teacher-forcing traces of the plain form (product_decode_ex only; the
+     batched forms ignore them).  Entry h-1 describes half iteration h; a
+     frame's entries past its last half are not written. */
+  float *le_trace;       /* device [2 max_iter][n_frames][n_col][n_row]: the
+                            extrinsic state L_E = L_APP - lambda after half h,
+                            row-major positions (Sec. V-B); the SISO input of
+                            half h+1 is lambda = fl32(L_Ch + fl32(alpha L_E)) */
+  int32_t *word_queries; /* device [2 max_iter][n_frames][max(n_row, n_col)]:
+                            queries of each word decoded in half h (rows in odd
+                            halves, columns in even ones; -1 for a non-finite
+                            input) */
 } product_decode_stats;
 
 /*
- * product_decode with optional statistics (stats may be NULL; same errors).
+ * product_decode with optional statistics and per-half traces (stats may be
+ * NULL; same errors).  With traces the call also copies the L_E state after
+ * every half (4 n^2 bytes a frame per half).
  */
 int product_decode_ex(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch,
                       int L, int64_t query_cap, float thr, float alpha, int max_iter, uint8_t *bits,
@@ -193,8 +225,9 @@ int product_decode_ex(sogrand_code *row_code, const sogrand_code *col_code, int6
  * last word of a half runs that frame's row/column check and either finishes
  * the frame or queues it for its next half.  No per-half launches and no
  * host round trips; every frame advances at its own pace.  Waits inside the
- * kernel are bounded: if the queue stays empty for about 2^22 polls while
- * frames are unfinished the kernel stops and the call returns
+ * kernel are bounded (sogrand_set_wait_limits): if a warp finds no work for
+ * 2 s of accumulated back-off while frames are unfinished, or cannot take its
+ * block's remaining-mass lock, the kernel stops and the call returns
  * SOGRAND_ETIMEOUT.  stats->timing_ms[0] is the kernel's device time;
  * launches counts 2 (queue set-up and the decoder).  Scratch, allocated
  * stream-ordered from the library's pool (see sogrand_release_cached): about
@@ -320,6 +353,8 @@ int product_decode_host(sogrand_code *row_code, const sogrand_code *col_code, in
  * nothing: no cudaMalloc, cudaFree or allocating library routine.
  *   arguments and results as for product_decode, except that half_iters,
  *   status and queries are required; every output is device memory.
+ *   Only square product codes of one code are accepted: row_code must be
+ *   col_code (any other pair returns SOGRAND_EUNSUPPORTED).
  *   The call is asynchronous on `stream` and always launches all 2 *
  *   max_iter half iterations (frames that finished are skipped).
  *   The first call on a device looks up the array's device address on that
@@ -331,7 +366,8 @@ int product_decode_host(sogrand_code *row_code, const sogrand_code *col_code, in
  *   call clears what must start at zero.  Calls that overlap on the GPU (on
  *   different streams, or from different threads) race on the array and
  *   produce wrong results; serialise them.
- * Errors: EINVAL also when n_frames needs more scratch than the array holds
+ * Errors: EUNSUPPORTED when row_code != col_code; EINVAL also when n_frames
+ * needs more scratch than the array holds
  * (the bound is 4 n^2 F + 8 n ceil(n/64) F + 16 F bytes plus up to 1280
  * bytes of alignment, within SOGRAND_NOALLOC_SCRATCH_BYTES; for n = 64 about
  * 1980 frames) or when the tables do not cover query_cap; EUNSUPPORTED,

@@ -11,6 +11,7 @@ Public entry points (same names as the C ABI in include/sogrand.h):
 * :func:`sogrand_trace_patterns` -- the device's canonical query order (test hook);
 * :func:`sogrand_release_cached` -- hand the decoders' pooled scratch back to the device;
 * :func:`sogrand_int_peak` -- the measured integer-pipe rate (the roofline's denominator);
+* :func:`sogrand_set_wait_limits` -- bounds of the decoders' device-side waits;
 * :mod:`calibration` -- predicted vs empirical list-BLER and BER (SOGRAND and Forney's approximation).
 
 All compute runs in hand-written CUDA kernels for sm_103a (libsogrand.so);
@@ -19,6 +20,7 @@ PyTorch only provides device memory and streams.
 from ._lib import (  # noqa: F401
     Code, FrameGroup, LIB_PATH, ProductStats, Server, SograndError, load, product_decode, product_decode_host,
     product_decode_mixed, sogrand_code_create, gldpc_decode,
-    sogrand_decode, sogrand_int_peak, sogrand_release_cached, sogrand_trace_patterns, strerror, unpack_bits,
+    sogrand_decode, sogrand_int_peak, sogrand_release_cached, sogrand_set_wait_limits, sogrand_trace_patterns,
+    strerror, unpack_bits, DEFAULT_LOCK_POLLS, DEFAULT_QUEUE_WAIT_US,
     unpack_words,
 )

@@ -25,7 +25,8 @@ _lib = None
 class ProductStats(C.Structure):
     """product_decode_stats of include/sogrand.h."""
     _fields_ = [("par_queries", C.c_void_p), ("weight_sum", C.c_void_p), ("xf_words", C.c_void_p),
-                ("timing_ms", C.POINTER(C.c_float)), ("launches", C.POINTER(C.c_int32))]
+                ("timing_ms", C.POINTER(C.c_float)), ("launches", C.POINTER(C.c_int32)),
+                ("le_trace", C.c_void_p), ("word_queries", C.c_void_p)]
 
 
 class SograndError(RuntimeError):
@@ -56,6 +57,7 @@ def load() -> C.CDLL:
         L.sogrand_code_destroy.restype = None
         L.sogrand_code_reserve.argtypes = [vp, i64]
         L.sogrand_code_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
+        L.sogrand_set_wait_limits.argtypes = [i64, i64, i32]
         L.sogrand_decode.argtypes = [vp, i64, vp, vp, i32, i64, f32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.sogrand_decode_forney.argtypes = [vp, i64, vp, vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.product_decode.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp]
@@ -81,7 +83,8 @@ def load() -> C.CDLL:
         L.sogrand_int_peak.argtypes = [i64, C.POINTER(C.c_double), C.POINTER(C.c_double), vp]
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
-        for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_decode",
+        for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_set_wait_limits",
+                     "sogrand_decode",
                      "sogrand_decode_forney",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
                      "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak",
@@ -207,11 +210,13 @@ def sogrand_decode(code: Code, llr_ch, llr_a=None, L: int = 4, query_cap: int = 
 
 def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
                    max_iter: int = 20, col_code: Code | None = None, stream=None, out=None, stats: bool = True,
-                   persistent: bool = False) -> dict:
+                   persistent: bool = False, trace: bool = False) -> dict:
     """Decode [F, n, n] frames (float32 CUDA tensor); returns CUDA tensors (and,
     with stats, host-side timing_ms / launches).  persistent=True uses the
     batched form (product_decode_persistent), else one launch per half
-    (product_decode_ex)."""
+    (product_decode_ex).  trace=True (plain form) also returns le_trace
+    [2 max_iter, F, n_col, n_row] (L_E after every half) and word_queries
+    [2 max_iter, F, max(n_row, n_col)] (queries of every word of every half)."""
     import torch
     cc = col_code if col_code is not None else code
     F, nc, nr = llr_ch.shape  # frames of n_col rows (column code's n) by n_row columns (row code's n)
@@ -226,11 +231,17 @@ def product_decode(code: Code, llr_ch, L: int = 4, query_cap: int = 10**4, thr: 
                    weight_sum=torch.zeros(1, dtype=torch.int64, device=dev),
                    xf_words=torch.zeros(1, dtype=torch.int32, device=dev))
     st = None
+    if trace:
+        assert not persistent, "per-half traces come from the plain form"
+        stats = True
+        out["le_trace"] = torch.full((2 * max_iter, F, nc, nr), float("nan"), dtype=torch.float32, device=dev)
+        out["word_queries"] = torch.full((2 * max_iter, F, max(nr, nc)), -2, dtype=torch.int32, device=dev)
     if stats:
         tm = (C.c_float * 2)()
         ln = (C.c_int32 * 1)()
         st = ProductStats(_ptr(out.get("par_queries")), _ptr(out.get("weight_sum")), _ptr(out.get("xf_words")),
-                          C.cast(tm, C.POINTER(C.c_float)), C.cast(ln, C.POINTER(C.c_int32)))
+                          C.cast(tm, C.POINTER(C.c_float)), C.cast(ln, C.POINTER(C.c_int32)),
+                          _ptr(out.get("le_trace")), _ptr(out.get("word_queries")))
     fn = load().product_decode_persistent if persistent else load().product_decode_ex
     rc = fn(code.handle, cc.handle, F, _ptr(llr_ch), int(L), int(query_cap), float(thr), float(alpha), int(max_iter),
             _ptr(out["bits"]), _ptr(out.get("half_iters")), _ptr(out.get("status")), _ptr(out.get("queries")),
@@ -385,6 +396,15 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def sogrand_set_wait_limits(queue_wait_us: int = -1, lock_polls: int = -1, lock_preheld: int = -1):
+    """Limits of the bounded device waits (negative: keep); see include/sogrand.h."""
+    _check(load().sogrand_set_wait_limits(int(queue_wait_us), int(lock_polls), int(lock_preheld)),
+           "sogrand_set_wait_limits")
+
+
+DEFAULT_QUEUE_WAIT_US, DEFAULT_LOCK_POLLS = 2_000_000, 1 << 22
 
 
 def sogrand_release_cached():

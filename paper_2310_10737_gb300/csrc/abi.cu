@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -36,6 +37,22 @@ constexpr int64_t MAX_CAP = int64_t(1) << 24;
 constexpr int64_t SAT = int64_t(1) << 60;
 
 inline int64_t sat_add(int64_t a, int64_t b) { return (a > SAT - b) ? SAT : a + b; }
+
+// Limits of the bounded device waits (sogrand_set_wait_limits), read when a
+// decode is launched: a persistent launch's warps give up after this much
+// accumulated back-off without work; a warp gives up on the block's
+// remaining-mass lock after lock_polls polls.
+std::atomic<int64_t> g_queue_wait_us{2000000};
+std::atomic<int64_t> g_lock_polls{int64_t(1) << 22};
+std::atomic<int> g_lock_preheld{0};
+
+sg::SisoParams siso_params(int L, int64_t cap, float thr, int forney = 0) {
+  sg::SisoParams P{L, (int32_t)cap, thr};
+  P.forney = forney;
+  P.lock_polls = (int32_t)g_lock_polls.load();
+  P.lock_preheld = g_lock_preheld.load();
+  return P;
+}
 
 // log(2^a - 1)
 double log_pow2m1(int a) { return a * std::log(2.0) + std::log1p(-std::ldexp(1.0, -a)); }
@@ -372,6 +389,8 @@ cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P
   SG_DISPATCH(c, e = (sg::launch_product_persistent<NPL, SYN, false>(d, d, P, a, s)));
   return e;
 }
+sg::SisoParams siso_params_of(int L, int64_t cap, float thr) { return siso_params(L, cap, thr); }
+int32_t queue_wait_us() { return (int32_t)g_queue_wait_us.load(); }
 int sm_count_of_device() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -482,6 +501,14 @@ int sogrand_code_info(const sogrand_code *c, int *n, int *k) {
   return SOGRAND_OK;
 }
 
+int sogrand_set_wait_limits(int64_t queue_wait_us, int64_t lock_polls, int lock_preheld) {
+  if (queue_wait_us > INT32_MAX || lock_polls > INT32_MAX || lock_preheld > 1) return SOGRAND_EINVAL;
+  if (queue_wait_us >= 0) g_queue_wait_us.store(queue_wait_us);
+  if (lock_polls >= 0) g_lock_polls.store(lock_polls);
+  if (lock_preheld >= 0) g_lock_preheld.store(lock_preheld);
+  return SOGRAND_OK;
+}
+
 }  // extern "C"
 
 namespace {
@@ -496,7 +523,7 @@ int decode_words(sogrand_code *c, int64_t n_words, const float *llr_ch, const fl
   int rc = ensure_cap(c, cap);
   if (rc != SOGRAND_OK) return rc;
   sg::DevCode d = dev_code(c);
-  sg::SisoParams P{L, (int32_t)cap, thr, forney};
+  sg::SisoParams P = siso_params(L, cap, thr, forney);
   sg::DecodeArgs a{n_words, llr_ch, llr_a, hard, llr_app, llr_ext, p_miss, queries, list_words, list_app, list_count,
                    nullptr};
   cudaError_t e;
@@ -581,7 +608,7 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   a.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
   sg::DevCode d = dev_code(c), dcol = dev_code(cc);
   const bool gen = cc != c || a.nr != a.nc;  // not the square product of one code
-  sg::SisoParams P{L, (int32_t)cap, thr};
+  sg::SisoParams P = siso_params(L, cap, thr);
   cudaError_t e = cudaSuccess;
   const bool timed = stats && stats->timing_ms;
   cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
@@ -590,13 +617,23 @@ int product_decode_ex(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, con
   int launches = 0;
   float t_half = 0.f, t_check = 0.f;
   if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_init<NPL, SYN>(d, a, s)));
+  float *le_trace = stats ? stats->le_trace : nullptr;
+  int32_t *wq_trace = stats ? stats->word_queries : nullptr;
+  const size_t nn = (size_t)nr * nc;
   for (int h = 1; h <= a.max_half && e == cudaSuccess; h++) {
+    // teacher-forcing traces: this half's per-word query counts go straight to
+    // their slice; the L_E state is copied after the half
+    a.wq = wq_trace ? wq_trace + (size_t)(h - 1) * F * hbw : nullptr;
     if (timed) e = cudaEventRecord(ev[0], s);
     if (e == cudaSuccess)
       SG_DISPATCH(c, e = (gen ? sg::launch_product_half<NPL, SYN, true>(d, dcol, P, a, h, s)
                               : sg::launch_product_half<NPL, SYN, false>(d, dcol, P, a, h, s)));
     if (e != cudaSuccess) break;
     launches++;
+    if (le_trace)
+      e = cudaMemcpyAsync(le_trace + (size_t)(h - 1) * F * nn, a.le, (size_t)F * nn * sizeof(float),
+                          cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) break;
     if (timed) e = cudaEventRecord(ev[1], s);
     if (e == cudaSuccess) e = cudaMemsetAsync(a.active, 0, sizeof(int32_t), s);
     if (e == cudaSuccess) SG_DISPATCH(c, e = (sg::launch_product_check<NPL, SYN>(d, dcol, a, h, s)));
@@ -701,7 +738,7 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   a.queries = queries ? queries : q_s;
   a.par_queries = par_queries ? par_queries : pq_s;
   a.status = status ? status : st_s;
-  a.max_spin = 2000000;  // 2 s of back-off without any work
+  a.max_spin = (int32_t)g_queue_wait_us.load();  // back-off without any work before giving up
   a.xf_count = xf;
   a.wsum = wsum;
   *err_dev = a.ctrl + 3;
@@ -738,7 +775,7 @@ int persistent_decode(sogrand_code *rc_, const sogrand_code *cc_, int diag, int6
   char *mem = nullptr;
   if (scratch_alloc(&mem, persistent_scratch_bytes(F, c->n, cc->n, c->nm, max_iter), s) != cudaSuccess)
     return SOGRAND_ENOMEM;
-  const sg::SisoParams P{L, (int32_t)cap, thr};
+  const sg::SisoParams P = siso_params(L, cap, thr);
   const bool timed = stats && stats->timing_ms;
   cudaEvent_t ev[2] = {nullptr, nullptr};
   cudaError_t e = cudaSuccess;
@@ -864,7 +901,7 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   uint8_t *d_st = (uint8_t *)(mem + b_in + b_bits + al256((size_t)F * 4));
   int64_t *d_q = (int64_t *)(mem + b_in + b_bits + al256((size_t)F * 4) + al256((size_t)F));
   int32_t *d_err = (int32_t *)(mem + b_out + 2 * b_scr);  // one timeout flag per chunk (K <= 8)
-  const sg::SisoParams P{L, (int32_t)cap, thr};
+  const sg::SisoParams P = siso_params(L, cap, thr);
   cudaStream_t st[4] = {nullptr, nullptr, nullptr, nullptr};  // h2d, decode x2, d2h
   std::vector<cudaEvent_t> ev;
   cudaError_t e = cudaSuccess;
@@ -1005,7 +1042,7 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
     a.ctrl = (int32_t *)(mem + o_ctrl);  // a lock timeout in a word stops the launch
     sg::MixGroup &M = tab[g];
     M.code = dev_code(c);
-    M.P = sg::SisoParams{L, (int32_t)cap, thr};
+    M.P = siso_params(L, cap, thr);
     M.a = a;
     M.frames = nullptr;
     M.first = first;
@@ -1024,7 +1061,7 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   m.dpbytes = dpbytes;
   m.queue = (int32_t *)(mem + o_queue);
   m.ctrl = (int32_t *)(mem + o_ctrl);
-  m.max_spin = 2000000;
+  m.max_spin = (int32_t)g_queue_wait_us.load();
   m.xf_count = stats ? stats->xf_words : nullptr;
   m.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
   const bool timed = stats && stats->timing_ms;
@@ -1134,6 +1171,8 @@ int product_decode_noalloc(sogrand_code *rc_, const sogrand_code *cc_, int64_t F
     if (cap > c->tab_cap) return SOGRAND_EINVAL;
   }
   const int n = c->n, nm = c->nm;
+  // bound F before any product with it (a huge F must not wrap the size below)
+  if (F > (int64_t)(SOGRAND_NOALLOC_SCRATCH_BYTES / (4 * n * n + 8 * n * nm + 16))) return SOGRAND_EINVAL;
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t b_le = (size_t)F * n * n * sizeof(float), b_hb = (size_t)F * n * nm * sizeof(uint64_t);
   const size_t b_i32 = (size_t)F * sizeof(int32_t), b_i64 = (size_t)F * sizeof(int64_t);
@@ -1175,7 +1214,7 @@ int product_decode_noalloc(sogrand_code *rc_, const sogrand_code *cc_, int64_t F
   a.status = status;
   a.queries = queries;
   sg::DevCode d = dev_code(c);
-  sg::SisoParams P{L, (int32_t)cap, thr};
+  sg::SisoParams P = siso_params(L, cap, thr);
   // frame flags, per-half maxima and counters start at zero on every call
   // (the array keeps the previous call's contents)
   cudaError_t e = cudaSuccess;

@@ -35,9 +35,15 @@ __device__ __forceinline__ void bind_scratch(Scratch<NPL, SYN> &sc, unsigned cha
   sc.bind(smem + warp * wstride, smem + WARPS_PER_BLOCK * wstride, dpbytes);
 }
 
-// Clear the block's remaining-mass lock (every thread of the block calls this).
-__device__ __forceinline__ void init_block_lock(unsigned char *smem, int wstride, int dpbytes) {
-  if (threadIdx.x == 0) *reinterpret_cast<int *>(smem + WARPS_PER_BLOCK * wstride + dpbytes) = 0;
+// Clear the block's remaining-mass lock and store its poll limit (every
+// thread of the block calls this).  P.lock_preheld starts the block with the
+// lock taken, as if a warp held it and never released it.
+__device__ __forceinline__ void init_block_lock(unsigned char *smem, int wstride, int dpbytes, const SisoParams &P) {
+  if (threadIdx.x == 0) {
+    int *lock = reinterpret_cast<int *>(smem + WARPS_PER_BLOCK * wstride + dpbytes);
+    lock[0] = P.lock_preheld ? 1 : 0;
+    lock[1] = P.lock_polls;
+  }
   __syncthreads();
 }
 
@@ -48,7 +54,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const 
   using LY = Layout<NPL, SYN>;
   constexpr int NM = (32 * NPL + 63) / 64;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax), P);
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(code.jmax));
   const int n = code.n;
@@ -106,7 +112,7 @@ __global__ void k_trace(const DevCode code, const float *lam_in, int max_q, uint
   extern __shared__ __align__(16) unsigned char smem[];
   using LY = Layout<NPL, SYN>;
   const int lane = threadIdx.x & 31;
-  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax));
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(code.jmax), SisoParams{1, 1, 0.f});
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, 0, LY::warp_bytes, LY::dp_bytes(code.jmax));
   float lam[NPL];
@@ -231,6 +237,7 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
       if (2 * wd2 + 1 < NPL) v |= (uint64_t)hb[2 * wd2 + 1] << 32;
       dst[wd2] = v;
     }
+    if (a.wq) a.wq[(size_t)f * (GEN ? a.hbw : n) + wd] = res.queries;
     if (res.queries >= 0) {
       atomicAdd(reinterpret_cast<unsigned long long *>(a.queries + f), (unsigned long long)res.queries);
       atomicMax(a.hmax + f, res.queries);
@@ -368,7 +375,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode rowc, 
   using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int jm = max(rowc.jmax, colc.jmax);
-  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(jm));
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(jm), P);
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(jm));
   const DevCode &code = ROWS ? rowc : colc;  // the code of this half's words
@@ -543,7 +550,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
   using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int jm = max(rowc.jmax, colc.jmax);
-  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(jm));
+  init_block_lock(smem, LY::warp_bytes, LY::dp_bytes(jm), P);
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, LY::warp_bytes, LY::dp_bytes(jm));
   const int slot_n = GEN ? max(a.nr, a.nc) : rowc.n;  // tickets per list slot: the most words in a half
@@ -613,7 +620,7 @@ __global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
     int *dst = reinterpret_cast<int *>(tab);
     for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
   }
-  init_block_lock(smem, m.wstride, m.dpbytes);
+  init_block_lock(smem, m.wstride, m.dpbytes, m.groups[0].P);
   unsigned char *wsm = smem + warp * m.wstride;
   const int64_t nslots = m.total * (int64_t)m.max_half;
   unsigned long long *tslot = reinterpret_cast<unsigned long long *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16) + 2 * warp;

@@ -63,6 +63,8 @@ struct ProductArgs {
   int32_t *frame_list;        // [n_frames] or null: frames 0 .. n_frames-1, all new
   int32_t epoch_halves;       // > 0 with frame_list and half_stop
   int32_t grid_cap;           // > 0: at most this many blocks
+  // plain form only: query count of every word of the current half, [F][hbw] (or null)
+  int32_t *wq;
 };
 
 // Mixed form: groups of frames, one code per group, in one launch.

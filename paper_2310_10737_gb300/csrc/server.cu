@@ -41,6 +41,8 @@ int ensure_code_cap(sogrand_code *c, int64_t cap);
 cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P, const sg::ProductArgs &a,
                                   cudaStream_t s);
 int sm_count_of_device();
+sg::SisoParams siso_params_of(int L, int64_t cap, float thr);
+int32_t queue_wait_us();
 }  // namespace sgi
 
 namespace {
@@ -310,7 +312,7 @@ cudaError_t launch(sogrand_server *sv, Pool &p, int64_t total_words) {
   a.done_words = p.done_words;
   a.bad = p.bad;
   a.ctrl = p.ctrl;
-  a.max_spin = 2000000;
+  a.max_spin = sgi::queue_wait_us();
   a.half_stop = p.half_stop;
   a.frame_list = p.list;
   a.epoch_halves = sv->epoch_halves;
@@ -318,7 +320,7 @@ cudaError_t launch(sogrand_server *sv, Pool &p, int64_t total_words) {
   const int64_t words = F * p.n;
   const int64_t full = (int64_t)sgi::sm_count_of_device() * 8;
   a.grid_cap = (int)std::max<int64_t>(full / 8, total_words > 0 ? (full * words + total_words - 1) / total_words : full);
-  const sg::SisoParams P{sv->L, (int32_t)sv->cap, sv->thr};
+  const sg::SisoParams P = sgi::siso_params_of(sv->L, sv->cap, sv->thr);
   if (e == cudaSuccess) e = sgi::launch_persistent_for(p.code, P, a, p.stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p.h_status, p.status, p.slots, cudaMemcpyDeviceToHost, p.stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(p.h_ctrl, p.ctrl, 16, cudaMemcpyDeviceToHost, p.stream);

@@ -44,7 +44,9 @@ struct SisoParams {
   int32_t L;
   int32_t cap;
   float thr;
-  int32_t forney;  // 1: Forney's list-only normalisation (the mass outside the list taken as 0)
+  int32_t forney = 0;            // 1: Forney's list-only normalisation (the mass outside the list taken as 0)
+  int32_t lock_polls = 1 << 22;  // polls of the block's remaining-mass lock before a warp gives up on it
+  int32_t lock_preheld = 0;      // 1: blocks start with that lock taken (test of the bound)
 };
 
 // Per-word results that the callers write out.

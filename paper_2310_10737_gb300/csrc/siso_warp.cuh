@@ -196,7 +196,8 @@ struct RankRec {
 // of component decodings), then a tail: the area's lock word (16 bytes) and
 // one 16-byte tally slot per warp (summed pattern weights, extended-range
 // words), flushed to global counters when the warp exits.
-// lock word + one tally slot per warp, after the block's remaining-mass area
+// lock word (and, after it, the lock's poll limit) + one tally slot per warp,
+// after the block's remaining-mass area
 constexpr int TAIL_BYTES = 16 + 16 * WARPS_PER_BLOCK;
 
 template <int NPL, class SYN>
@@ -260,15 +261,17 @@ struct Scratch {
 
 // The block's remaining-mass area is taken by one warp at a time.  Its holder
 // runs a bounded computation that waits for nothing, so the wait ends; the
-// bound (about 4 s) only keeps a broken state from spinning for ever: the
-// warp then proceeds without the lock and reports it (returns false).
+// bound (lock[1] polls, about 4 s by default) only keeps a broken state from
+// spinning for ever: the warp then proceeds without the lock and reports it
+// (returns false).
 __device__ __forceinline__ bool dp_lock(int *lock, int lane) {
   int ok = 1;
   if (lane == 0) {
     unsigned nap = 32;
     long long tries = 0;
+    const long long limit = *reinterpret_cast<volatile int *>(lock + 1);
     while (atomicCAS(lock, 0, 1) != 0) {
-      if (++tries > (1ll << 22)) {
+      if (++tries > limit) {
         ok = 0;
         break;
       }

@@ -7,8 +7,9 @@ The entry point is called through the C ABI and must give exactly what
 product_decode gives (the same kernels: bit-exact frames, half iterations,
 status and query counts), on two calls in a row with different batches, so a
 stale array from the first call would show in the second.  It must also
-refuse batches larger than the array and query caps its tables do not cover,
-writing nothing.  This file is collected last so that a failure here leaves
+refuse batches larger than the array (also frame counts whose scratch size
+would overflow), query caps its tables do not cover and row and column codes
+that differ, writing nothing.  This file is collected last so that a failure here leaves
 every other test already run; it passes alone and after the others.
 """
 import ctypes as C
@@ -39,7 +40,7 @@ def env():
     return torch, sg, lib
 
 
-def _noalloc(env, code_h, lch, L=4, cap=10**4, alpha=0.5, max_iter=4, fill=None):
+def _noalloc(env, code_h, lch, L=4, cap=10**4, alpha=0.5, max_iter=4, col_h=None, n_frames=None):
     torch, sg, lib = env
     F, n, _ = lch.shape
     dev = lch.device
@@ -48,7 +49,8 @@ def _noalloc(env, code_h, lch, L=4, cap=10**4, alpha=0.5, max_iter=4, fill=None)
                status=torch.full((F,), 9, dtype=torch.uint8, device=dev),
                queries=torch.full((F,), -5, dtype=torch.int64, device=dev))
     s = C.c_void_p(torch.cuda.current_stream().cuda_stream)
-    rc = lib.product_decode_noalloc(code_h, code_h, F, C.c_void_p(lch.data_ptr()), L, cap, 0.0, alpha, max_iter,
+    rc = lib.product_decode_noalloc(code_h, code_h if col_h is None else col_h, F if n_frames is None else n_frames,
+                                    C.c_void_p(lch.data_ptr()), L, cap, 0.0, alpha, max_iter,
                                     C.c_void_p(out["bits"].data_ptr()), C.c_void_p(out["half_iters"].data_ptr()),
                                     C.c_void_p(out["status"].data_ptr()), C.c_void_p(out["queries"].data_ptr()), s)
     torch.cuda.synchronize()
@@ -86,6 +88,14 @@ def test_noalloc_refuses_oversized_batches_and_uncovered_caps(env):
     small = torch.zeros((4, n, n), dtype=torch.float32, device="cuda")
     rc, got = _noalloc(env, c.handle, small, cap=10**4 + 1)  # the tables cover 10^4 only
     assert rc == 1 and (got["status"] == 9).all()
+    # a frame count so large that the scratch size would wrap around 2^64
+    rc, got = _noalloc(env, c.handle, small, n_frames=1 << 62)
+    assert rc == 1 and (got["half_iters"] == -7).all() and (got["bits"] == 0xA5).all()
+    # only the square product of one code: another column code is refused
+    other = sg.Code.from_linear_code(ebch("ebch_64_51"))
+    rc, got = _noalloc(env, c.handle, small, col_h=other.handle)
+    assert rc == 5 and (got["queries"] == -5).all()  # SOGRAND_EUNSUPPORTED
+    other.close()
     fits = SCRATCH_BYTES // per_frame - 4
     rc, got = _noalloc(env, c.handle, torch.full((fits, n, n), 5.0, dtype=torch.float32, device="cuda"), max_iter=1)
     assert rc == 0 and (got["status"] == 0).all() and (got["half_iters"] == 1).all()
