@@ -281,6 +281,124 @@ def serving_bench(sg, torch, n_req, loads, seed, epoch_halves=2):
     return res
 
 
+def _events_ms(torch, fn, reps):
+    """Device time of `reps` calls of fn (CUDA events on the current stream,
+    synchronised on both sides), after one untimed call."""
+    fn()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        fn()
+    e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps
+
+
+def _frame_errors(bits_dev, X):
+    """Frames whose decoded (packed, LSB first) bits differ from the transmitted X [F, n, n]."""
+    ref = np.packbits(X.reshape(X.shape[0], -1), axis=1, bitorder="little")
+    return (bits_dev.cpu().numpy() != ref).any(axis=1)
+
+
+def other_configs(sg, torch, cores, reps=2):
+    """The other workloads of the method, measured beside the headline (each
+    a separate figure, not part of `value`):
+    C1  plain method: eBCH(32,26)^2, 200 frames at 3.0 dB, L=4, cap 1e4, 4 iterations;
+    C2  component SISO: 10^6 eBCH(64,57) and 10^6 eBCH(32,26) words, Eb/N0 2/3/4/5 dB
+        (word w at point w mod 4), L in {1, 2, 4}, cap 1e5, one launch per code and L;
+    C4  mixed batch: 200,000 frames of eBCH(32,26)^2, (64,51)^2, (128,120)^2 in 4:2:1,
+        Eb/N0 uniform in 2.5..4.0 dB per frame, L=4, cap 1e4, 20 iterations: one mixed
+        launch vs the batched form per code vs the plain form per code."""
+    from workloads import awgn_frames, awgn_words, ebch
+    res = {}
+    dev = torch.device("cuda")
+    # C1
+    code = ebch("ebch_32_26")
+    U, X, lch = awgn_frames(code, 200, 3.0, seed=1, threads=cores)
+    c = sg.Code.from_linear_code(code)
+    d = torch.from_numpy(lch).to(dev)
+    kw = dict(L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=4, stats=False)
+    c1 = {"workload": "eBCH(32,26)^2, 200 frames, 3.0 dB, L=4, cap 1e4, alpha 0.5, 4 iterations", "frames": 200}
+    for form, pers in (("plain", False), ("persistent", True)):
+        box = {}
+        ms = _events_ms(torch, lambda: box.update(o=sg.product_decode(c, d, persistent=pers, **kw)), reps + 3)
+        c1[form] = {"ms": ms, "bits_per_s": 200 * 26 * 26 / (ms / 1000),
+                    "bler": float(_frame_errors(box["o"]["bits"], X).mean())}
+    c.close()
+    res["C1"] = c1
+    log(f"C1: plain {c1['plain']['ms']:.2f} ms, persistent {c1['persistent']['ms']:.2f} ms")
+    # C2
+    W = 10**6
+    snr = np.array([2.0, 3.0, 4.0, 5.0])[np.arange(W) % 4]
+    c2 = {"workload": "10^6 words per code, Eb/N0 2/3/4/5 dB (word w at point w mod 4), component rate, "
+                      "L in {1,2,4}, cap 1e5, one sogrand_decode launch per code and L", "words": W}
+    for name in ("ebch_64_57", "ebch_32_26"):
+        code = ebch(name)
+        _, _, lw = awgn_words(code, W, snr, seed=2, threads=cores)
+        c = sg.Code.from_linear_code(code)
+        c.reserve(10**5)
+        cap_t, tbytes = c.tables()
+        d = torch.from_numpy(lw).to(dev)
+        row = {"table_bytes": tbytes, "table_cap": cap_t}
+        for L in (1, 2, 4):
+            box = {}
+            ms = _events_ms(torch, lambda: box.update(o=sg.sogrand_decode(c, d, L=L, query_cap=10**5, lists=False)),
+                            reps)
+            q = int(box["o"]["queries"].sum())
+            row[f"L{L}"] = {"ms": ms, "words_per_s": W / (ms / 1000), "queries_per_s": q / (ms / 1000),
+                            "info_bits_per_s": W * code.k / (ms / 1000), "queries_per_word": q / W}
+        c2[name] = row
+        c.close()
+        del d
+        log(f"C2 {name}: " + ", ".join(f"L={L} {row[f'L{L}']['ms']:.1f} ms" for L in (1, 2, 4)))
+    res["C2"] = c2
+    # C4
+    names = ["ebch_32_26", "ebch_64_51", "ebch_128_120"]
+    total = 200_000
+    counts = [total * 4 // 7, total * 2 // 7]
+    counts.append(total - sum(counts))
+    rng = np.random.default_rng(SEED + 4)
+    groups, refs, codes = [], [], []
+    info = 0
+    for i, (name, F) in enumerate(zip(names, counts)):
+        code = ebch(name)
+        snr = rng.uniform(2.5, 4.0, F)
+        U, X, lf = awgn_frames(code, F, snr, seed=SEED + 40 + i, threads=cores)
+        c = sg.Code.from_linear_code(code)
+        d = torch.from_numpy(lf).to(dev)
+        del lf
+        c.tune(d[:4000], L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER)
+        groups.append((c, d))
+        refs.append(X)
+        codes.append(code)
+        info += F * code.k * code.k
+    kw = dict(L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER)
+    c4 = {"workload": f"{total} frames, eBCH(32,26)^2 : (64,51)^2 : (128,120)^2 = 4:2:1 "
+                      f"({counts[0]} + {counts[1]} + {counts[2]}), Eb/N0 uniform 2.5..4.0 dB per frame, L=4, "
+                      "cap 1e4, alpha 0.5, max 20 iterations", "frames": total, "info_bits": info,
+          "schedules": {nm: c.schedule() for nm, (c, _) in zip(names, groups)}}
+    box = {}
+    ms = _events_ms(torch, lambda: box.update(o=sg.product_decode_mixed(groups, stats=False, **kw)[0]), reps)
+    c4["mixed"] = {"ms": ms, "bits_per_s": info / (ms / 1000), "launches": 2,
+                   "bler": {nm: float(_frame_errors(o["bits"], X).mean()) for nm, o, X in zip(names, box["o"], refs)}}
+    for form, pers in (("batched_per_code", True), ("plain_per_code", False)):
+        box = {}
+
+        def per_code():
+            box["o"] = [sg.product_decode(c, d, persistent=pers, stats=False, **kw) for c, d in groups]
+
+        ms = _events_ms(torch, per_code, reps)
+        c4[form] = {"ms": ms, "bits_per_s": info / (ms / 1000),
+                    "bler": {nm: float(_frame_errors(o["bits"], X).mean()) for nm, o, X in zip(names, box["o"], refs)}}
+    log("C4: " + ", ".join(f"{f} {c4[f]['ms']:.1f} ms" for f in ("mixed", "batched_per_code", "plain_per_code")))
+    for c, _ in groups:
+        c.close()
+    res["C4"] = c4
+    return res
+
+
 def cpu_oracle_rate(code, lch, threads):
     """The oracle (FP64, plain C, all host cores) on a bounded sample: info bits/s."""
     import oracle
@@ -334,6 +452,7 @@ def main():
     ap.add_argument("--plain-steps", type=int, default=3, help="steps of the other form, timed for comparison (0: off)")
     ap.add_argument("--serve-requests", type=int, default=1200, help="requests per offered load in the serving run (0: off)")
     ap.add_argument("--serve-loads", default="250,500,1000,2000", help="offered loads, requests/s")
+    ap.add_argument("--other-configs", type=int, default=1, help="1: also measure the C1, C2 and C4 workloads")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -507,6 +626,10 @@ def main():
         serving = serving_bench(sg, torch, args.serve_requests, [float(x) for x in args.serve_loads.split(",")],
                                 SEED + 1000 + rank)
 
+    others = None
+    if rank == 0 and args.other_configs:
+        others = other_configs(sg, torch, cores)
+
     cpu = None
     if rank == 0 and world == 1 and args.cpu_frames > 0:
         rate, dt = cpu_oracle_rate(code, lch[: args.cpu_frames], cores)
@@ -521,7 +644,7 @@ def main():
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": workload_config(F),
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "queries_per_s": world * qtot / (ms / 1000), "xf_words": int(out["xf_words"].item()),
-                "quality": quality, "serving": serving,
+                "quality": quality, "serving": serving, "other_configs": others,
                 "schedule": {"blocks_per_sm": sched, "tuned_on": f"{min(F, 10_000)} frames",
                              "sample_ms": {"6": sched_ms[0], "8": sched_ms[1]}},
                 "form": ("persistent (one kernel per decode, device-side frame queue)" if main_persistent

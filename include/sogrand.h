@@ -80,6 +80,10 @@ int sogrand_code_reserve(sogrand_code *code, int64_t max_query_cap);
 /* Length n and dimension k of a code (either pointer may be NULL). */
 int sogrand_code_info(const sogrand_code *code, int *n, int *k);
 
+/* The query-order tables of a code: the query cap they cover and their
+ * device memory in bytes (either pointer may be NULL).  Errors: EINVAL. */
+int sogrand_code_tables(const sogrand_code *code, int64_t *query_cap, int64_t *bytes);
+
 /*
  * Limits of the bounded device-side waits (process-wide; read when a decode
  * is launched, so set them while no decode is being launched).  The paper has

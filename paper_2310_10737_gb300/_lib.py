@@ -58,6 +58,7 @@ def load() -> C.CDLL:
         L.sogrand_code_reserve.argtypes = [vp, i64]
         L.sogrand_code_info.argtypes = [vp, C.POINTER(C.c_int), C.POINTER(C.c_int)]
         L.sogrand_set_wait_limits.argtypes = [i64, i64, i32]
+        L.sogrand_code_tables.argtypes = [vp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
         L.sogrand_decode.argtypes = [vp, i64, vp, vp, i32, i64, f32, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.sogrand_decode_forney.argtypes = [vp, i64, vp, vp, i32, i64, vp, vp, vp, vp, vp, vp, vp, vp, vp]
         L.product_decode.argtypes = [vp, vp, i64, vp, i32, i64, f32, f32, i32, vp, vp, vp, vp, vp]
@@ -84,7 +85,7 @@ def load() -> C.CDLL:
         L.sogrand_strerror.argtypes = [i32]
         L.sogrand_strerror.restype = C.c_char_p
         for name in ("sogrand_code_create", "sogrand_code_reserve", "sogrand_code_info", "sogrand_set_wait_limits",
-                     "sogrand_decode",
+                     "sogrand_code_tables", "sogrand_decode",
                      "sogrand_decode_forney",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
                      "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak",
@@ -143,6 +144,12 @@ class Code:
 
     def reserve(self, max_query_cap: int):
         _check(load().sogrand_code_reserve(self._h, int(max_query_cap)), "sogrand_code_reserve")
+
+    def tables(self):
+        """(query cap the order tables cover, their device bytes)."""
+        cap, nb = C.c_int64(0), C.c_int64(0)
+        _check(load().sogrand_code_tables(self._h, C.byref(cap), C.byref(nb)), "sogrand_code_tables")
+        return cap.value, nb.value
 
     def schedule(self, minb: int = 0) -> int:
         """Set (6 or 8) or query (0) the blocks per SM the decoding kernels run at."""

@@ -375,6 +375,16 @@ int ensure_cap(sogrand_code *c, int64_t cap) {
 
 }  // namespace
 
+#ifdef SG_PHASE_PROFILE
+namespace sg {
+std::vector<PhaseReader> &phase_readers() {
+  static std::vector<PhaseReader> v;
+  return v;
+}
+void phase_register(PhaseReader r) { phase_readers().push_back(r); }
+}  // namespace sg
+#endif
+
 // Accessors for the serving loop (server.cu), which sees codes only through these.
 namespace sgi {
 sg::DevCode dev_code_of(const sogrand_code *c) { return dev_code(c); }
@@ -498,6 +508,14 @@ int sogrand_code_info(const sogrand_code *c, int *n, int *k) {
   if (!c) return SOGRAND_EINVAL;
   if (n) *n = c->n;
   if (k) *k = c->k;
+  return SOGRAND_OK;
+}
+
+int sogrand_code_tables(const sogrand_code *c, int64_t *query_cap, int64_t *bytes) {
+  if (!c) return SOGRAND_EINVAL;
+  std::lock_guard<std::mutex> g(const_cast<sogrand_code *>(c)->mu);
+  if (query_cap) *query_cap = c->tab_cap;
+  if (bytes) *bytes = c->tab_bytes;
   return SOGRAND_OK;
 }
 
@@ -1229,14 +1247,13 @@ int product_decode_noalloc(sogrand_code *rc_, const sogrand_code *cc_, int64_t F
 }
 
 #ifdef SG_PHASE_PROFILE
-// phase counters of the profiling build (not part of the public ABI)
+// phase counters of the profiling build (not part of the public ABI): the sum
+// over the translation units that registered a reader
 int sogrand_debug_phase(unsigned long long *out, int reset) {
-  cudaError_t e = cudaMemcpyFromSymbol(out, sg::g_phase, sizeof(unsigned long long) * 16);
-  if (reset) {
-    unsigned long long z[16] = {0};
-    cudaMemcpyToSymbol(sg::g_phase, z, sizeof(z));
-  }
-  return e == cudaSuccess ? 0 : SOGRAND_ECUDA;
+  for (int i = 0; i < 16; i++) out[i] = 0;
+  int bad = 0;
+  for (sg::PhaseReader r : sg::phase_readers()) bad |= r(out, reset);
+  return bad ? SOGRAND_ECUDA : 0;
 }
 #endif
 

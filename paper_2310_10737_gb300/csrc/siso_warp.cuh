@@ -50,8 +50,27 @@ namespace sg {
 #ifdef SG_PHASE_PROFILE
 // [0] prologue cycles [1] query-loop cycles [2] remainder cycles [3] soft-output
 // cycles [4] words [5] query chunks [6] - [7] DP ranks [8] XF fallbacks [9] smem DP
+// Every translation unit has its own copy of the counters (no relocatable
+// device code), so each registers a reader that sogrand_debug_phase sums.
 __device__ unsigned long long g_phase[16];
 #define SG_PROF(i, v) atomicAdd(&g_phase[i], (unsigned long long)(v))
+typedef int (*PhaseReader)(unsigned long long *acc, int reset);
+void phase_register(PhaseReader r);
+namespace {
+int phase_read_here(unsigned long long *acc, int reset) {
+  unsigned long long v[16];
+  if (cudaMemcpyFromSymbol(v, g_phase, sizeof(v)) != cudaSuccess) return 1;
+  for (int i = 0; i < 16; i++) acc[i] += v[i];
+  if (reset) {
+    unsigned long long z[16] = {0};
+    if (cudaMemcpyToSymbol(g_phase, z, sizeof(z)) != cudaSuccess) return 1;
+  }
+  return 0;
+}
+struct PhaseHook {
+  PhaseHook() { phase_register(phase_read_here); }
+} phase_hook_;
+}  // namespace
 #else
 #define SG_PROF(i, v) ((void)0)
 #endif
