@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <memory>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -985,7 +986,7 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   static_assert(SOGRAND_MIX_MAX_GROUPS == sg::MIX_MAX_GROUPS, "group table size");
   if (n_groups < 1 || n_groups > SOGRAND_MIX_MAX_GROUPS || !groups) return SOGRAND_EINVAL;
   int64_t total = 0;
-  int slot_n = 0, syn64 = -1;
+  int syn64 = -1;
   for (int g = 0; g < n_groups; g++) {
     const sogrand_frame_group &G = groups[g];
     int rc = persistent_check(G.code, G.code, G.n_frames, L, cap, thr, alpha, max_iter);
@@ -995,7 +996,6 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
     if (syn64 >= 0 && s64 != syn64) return SOGRAND_EUNSUPPORTED;  // one syndrome width per launch
     syn64 = s64;
     total += G.n_frames;
-    slot_n = std::max(slot_n, G.code->n);
   }
   if (total * 2 * (int64_t)max_iter * 128 >= (int64_t(1) << 31) - (int64_t(1) << 22)) return SOGRAND_EINVAL;
   if (total == 0) return SOGRAND_OK;
@@ -1005,29 +1005,68 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   }
   cudaStream_t s = (cudaStream_t)stream;
   const int max_half = 2 * max_iter;
-  // scratch: per group the persistent-form buffers, then the shared list,
-  // the control words and the device copy of the group table
-  std::vector<size_t> off(n_groups);
+  auto npl_of = [](int n) { return n <= 32 ? 1 : (n <= 64 ? 2 : 4); };
+  // groups with frames, ordered by class (lane layout), then as given
+  std::vector<int> order;
+  for (int npl : {1, 2, 4})
+    for (int g = 0; g < n_groups; g++)
+      if (groups[g].n_frames > 0 && npl_of(groups[g].code->n) == npl) order.push_back(g);
+  const int ng = (int)order.size();
+  // scratch: per group the persistent-form buffers, then per class its list
+  // and control words, then the launch's error word
+  std::vector<size_t> off(ng);
   size_t bytes = 0;
-  for (int g = 0; g < n_groups; g++) {
-    off[g] = bytes;
-    bytes += al256(persistent_scratch_bytes(groups[g].n_frames, groups[g].code->n, groups[g].code->n,
-                                            groups[g].code->nm, max_iter));
+  for (int x = 0; x < ng; x++) {
+    const sogrand_frame_group &G = groups[order[x]];
+    off[x] = bytes;
+    bytes += al256(persistent_scratch_bytes(G.n_frames, G.code->n, G.code->n, G.code->nm, max_iter));
   }
-  const size_t o_queue = bytes, o_ctrl = o_queue + al256((size_t)total * max_half * sizeof(int32_t));
-  const size_t o_tab = o_ctrl + 256, total_bytes = o_tab + al256(n_groups * sizeof(sg::MixGroup));
+  std::unique_ptr<sg::MixArgs> mp(new (std::nothrow) sg::MixArgs());
+  if (!mp) return SOGRAND_ENOMEM;
+  sg::MixArgs &m = *mp;
+  int ncls = 0, wstride = 0, dpbytes = 0, all8 = 1;
+  double work[sg::MIX_MAX_CLASSES] = {0, 0, 0};
+  size_t o_queue[sg::MIX_MAX_CLASSES] = {0, 0, 0}, o_ctrl[sg::MIX_MAX_CLASSES] = {0, 0, 0};
+  for (int x = 0; x < ng; x++) {
+    const sogrand_frame_group &G = groups[order[x]];
+    const int npl = npl_of(G.code->n);
+    if (x == 0 || npl != m.cls[ncls - 1].npl) {
+      sg::MixClass &C = m.cls[ncls++];
+      C = sg::MixClass{};
+      C.npl = npl;
+      C.g0 = C.g1 = x;
+    }
+    sg::MixClass &C = m.cls[ncls - 1];
+    m.groups[x].first = C.total;
+    C.total += G.n_frames;
+    C.g1 = x + 1;
+    C.slot_n = std::max(C.slot_n, G.code->n);
+    // estimated work of the class: coded bits times word length (sets the home classes only)
+    work[ncls - 1] += (double)G.n_frames * G.code->n * G.code->n * G.code->n;
+    all8 = all8 && G.code->minb == 8;
+  }
+  for (int c = 0; c < ncls; c++) {
+    o_queue[c] = bytes;
+    bytes += al256((size_t)m.cls[c].total * max_half * sizeof(int32_t));
+    o_ctrl[c] = bytes;
+    bytes += 256;
+  }
+  const size_t o_err = bytes;
+  bytes += 256;
   char *mem = nullptr;
-  if (scratch_alloc(&mem, total_bytes, s) != cudaSuccess) return SOGRAND_ENOMEM;
-  sg::MixGroup tab[SOGRAND_MIX_MAX_GROUPS] = {};
-  int wstride = 0, dpbytes = 0;
-  int64_t first = 0;
-  for (int g = 0; g < n_groups; g++) {
-    const sogrand_frame_group &G = groups[g];
+  if (scratch_alloc(&mem, bytes, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  for (int c = 0; c < ncls; c++) {
+    m.cls[c].queue = (int32_t *)(mem + o_queue[c]);
+    m.cls[c].ctrl = (int32_t *)(mem + o_ctrl[c]);
+  }
+  int32_t *gctrl = (int32_t *)(mem + o_err);  // [3]: the launch's error word
+  for (int x = 0; x < ng; x++) {
+    const sogrand_frame_group &G = groups[order[x]];
     sogrand_code *c = G.code;
-    const int npl = c->n <= 32 ? 1 : (c->n <= 64 ? 2 : 4);
+    const int npl = npl_of(c->n);
     wstride = std::max(wstride, sg::warp_area_bytes(npl, syn64 ? 8 : 4));
     dpbytes = std::max(dpbytes, sg::dp_area_bytes(npl, syn64 ? 8 : 4, c->jmax));
-    char *p = mem + off[g];
+    char *p = mem + off[x];
     auto take = [&p](size_t b) {
       char *r = p;
       p += al256(b);
@@ -1057,42 +1096,49 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
     a.par_queries = pq_s;
     a.status = G.status ? G.status : st_s;
     a.nr = a.nc = a.hbw = c->n;
-    a.ctrl = (int32_t *)(mem + o_ctrl);  // a lock timeout in a word stops the launch
-    sg::MixGroup &M = tab[g];
+    a.ctrl = gctrl;  // a remaining-mass lock timeout in a word sets gctrl[3] and stops the launch
+    sg::MixGroup &M = m.groups[x];
     M.code = dev_code(c);
     M.P = siso_params(L, cap, thr);
     M.a = a;
     M.frames = nullptr;
-    M.first = first;
     M.count = F;
     M.npl = npl;
     M.fresh = 1;
-    first += F;
   }
-  sg::MixArgs m{};
-  m.groups = (const sg::MixGroup *)(mem + o_tab);
-  m.ngroups = n_groups;
-  m.total = total;
-  m.slot_n = slot_n;
+  m.ngroups = ng;
+  m.ncls = ncls;
   m.max_half = max_half;
   m.wstride = wstride;
   m.dpbytes = dpbytes;
-  m.queue = (int32_t *)(mem + o_queue);
-  m.ctrl = (int32_t *)(mem + o_ctrl);
   m.max_spin = (int32_t)g_queue_wait_us.load();
+  m.err = gctrl + 3;
   m.xf_count = stats ? stats->xf_words : nullptr;
   m.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
+  // home classes: SM ids spread over the classes in proportion to their
+  // estimated work (a golden-ratio sequence, so that any subset of ids is
+  // split in about the same proportion)
+  double wsum = 0;
+  for (int c = 0; c < ncls; c++) wsum += work[c];
+  for (int t = 0; t < sg::MIX_SM_TABLE; t++) {
+    const double u = std::fmod(0.6180339887498949 * (t + 1), 1.0) * wsum;
+    double acc = 0;
+    int c = 0;
+    while (c + 1 < ncls && u >= acc + work[c]) acc += work[c++];
+    m.home[t] = (uint8_t)c;
+  }
   const bool timed = stats && stats->timing_ms;
   cudaEvent_t ev[2] = {nullptr, nullptr};
-  cudaError_t e = cudaMemcpyAsync(mem + o_tab, tab, n_groups * sizeof(sg::MixGroup), cudaMemcpyHostToDevice, s);
+  cudaError_t e = cudaSuccess;
   if (timed)
     for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
   if (e == cudaSuccess && timed) e = cudaEventRecord(ev[0], s);
   if (e == cudaSuccess)
-    e = syn64 ? sg::launch_product_mixed<uint64_t>(m, tab, 0, s) : sg::launch_product_mixed<uint32_t>(m, tab, 0, s);
+    e = syn64 ? sg::launch_product_mixed<uint64_t, 6>(m, 0, s)
+              : (all8 ? sg::launch_product_mixed<uint32_t, 8>(m, 0, s) : sg::launch_product_mixed<uint32_t, 6>(m, 0, s));
   if (e == cudaSuccess && timed) e = cudaEventRecord(ev[1], s);
   int32_t err = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, m.ctrl + 3, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, m.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && timed) {
     float x = 0.f;

@@ -2,6 +2,6 @@
 #include "kernels.cuh"
 
 namespace sg {
-template cudaError_t launch_product_mixed<uint32_t>(const MixArgs &, const MixGroup *, int, cudaStream_t);
-template cudaError_t launch_product_mixed<uint64_t>(const MixArgs &, const MixGroup *, int, cudaStream_t);
+template cudaError_t launch_product_mixed<uint32_t, 6>(const MixArgs &, int, cudaStream_t);
+template cudaError_t launch_product_mixed<uint64_t, 6>(const MixArgs &, int, cudaStream_t);
 }  // namespace sg

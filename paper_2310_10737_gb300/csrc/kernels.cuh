@@ -164,6 +164,7 @@ __device__ __forceinline__ void tally_flush(const unsigned long long *slot, unsi
 struct WordCtx {
   int64_t f, li;
   int32_t wd, half;
+  int32_t grp;  // mixed form: the word's group
 };
 static_assert(sizeof(WordCtx) <= 32, "the word's lambda follows the context in the frame-check area");
 
@@ -438,14 +439,16 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode rowc, const
 // -(e + 1) for an even one: the slot itself says which half it is, so a
 // ticket that the half skips (codes of different lengths) is recognised even
 // after the frame has moved on to its next half.  Returns 1 with *f1 = the
-// signed slot value, or 0 when the launch is over (every frame finished or parked, or the error flag is set).  The
-// wait backs off exponentially and gives up after max_spin microseconds of
-// sleep, setting the error flag.  All reads of shared state are made by lane 0
-// and broadcast, so the whole warp takes the same branch.
-__device__ __forceinline__ int sched_take(int32_t *ctrl_w, const volatile int32_t *queue, int64_t nslots,
-                                          int64_t frames, int slot_n, int max_spin, int lane, int *slot_out,
-                                          int *word_out, int *f1_out) {
-  volatile int32_t *ctrl = ctrl_w;  // [0] slots reserved, [1] word tickets, [2] finished frames, [3] error
+// signed slot value, or 0 when the list is done (every frame finished or
+// parked) or the launch's error word *err_w is set.  The wait backs off
+// exponentially and gives up after max_spin microseconds of sleep, setting
+// the error word.  All reads of shared state are made by lane 0 and
+// broadcast, so the whole warp takes the same branch.
+__device__ __forceinline__ int sched_take(int32_t *ctrl_w, int32_t *err_w, const volatile int32_t *queue,
+                                          int64_t nslots, int64_t frames, int slot_n, int max_spin, int lane,
+                                          int *slot_out, int *word_out, int *f1_out) {
+  volatile int32_t *ctrl = ctrl_w;  // [0] slots reserved, [1] word tickets, [2] finished frames
+  const volatile int32_t *err = err_w;
   int ticket = 0;
   if (lane == 0) ticket = atomicAdd(ctrl_w + 1, 1);
   ticket = __shfl_sync(FULL, ticket, 0);
@@ -455,7 +458,7 @@ __device__ __forceinline__ int sched_take(int32_t *ctrl_w, const volatile int32_
   unsigned nap = 64;
   for (;;) {
     if (lane == 0) {
-      if (ctrl[3] != 0) {
+      if (*err != 0) {
         st = 2;
       } else if (slot < nslots && (f1 = queue[slot]) != 0) {
         st = 1;
@@ -468,7 +471,7 @@ __device__ __forceinline__ int sched_take(int32_t *ctrl_w, const volatile int32_
     st = __shfl_sync(FULL, st, 0);
     if (st != 0) break;
     if (slept > (long long)max_spin * 1000) {
-      if (lane == 0) atomicExch(ctrl_w + 3, 1);
+      if (lane == 0) atomicExch(err_w, 1);
       st = 2;
       break;
     }
@@ -558,7 +561,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
   tally_clear(sc.tally(), lane);
   for (;;) {
     int slot, w, f1;
-    if (!sched_take(a.ctrl, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1)) break;
+    if (!sched_take(a.ctrl, a.ctrl + 3, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1)) break;
     const bool rows = f1 > 0;                      // the slot's half is odd: a row half
     int64_t li = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // list index
     const DevCode &code = GEN ? (rows ? rowc : colc) : rowc, &xcode = GEN ? (rows ? colc : rowc) : rowc;
@@ -591,95 +594,114 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
 }
 
 // ---- mixed form: frames of several codes (uneven n) in one launch ----
-// Groups of frames, one code each, share one frame-half list and ticket
-// counter.  List entry e (1-based) is frame e - 1 of the launch, i.e. entry
-// li = e - 1 - first of the group whose range holds it, and that group's
-// frame (buffer index) frames[li] (li when frames is null).  Slots hold
-// slot_n = the largest n of the launch word tickets; tickets past a frame's n
-// are skipped.  The SISO and the frame check run the instantiation of the
-// group's lanes-per-bit count NPL.
-template <class SYN, int NPL>
-__device__ __forceinline__ int mixed_word(const MixGroup &G, unsigned char *smem, int warp, int wstride, int dpbytes,
-                                          int64_t f, int w, int half, int lane) {
-  Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, wstride, dpbytes);
-  const int q = product_word<NPL, SYN, true, false, false>(G.code, G.P, G.a, sc, f, w, half, lane);
-  return q;
-}
+// The groups (one code each) are split into classes by lane layout; every
+// class has its own frame-half list and ticket counter, exactly as a
+// persistent launch of its own, and runs the instantiation of its NPL.  Every
+// SM has a home class (by %smid): its warps take tickets of that class while
+// the class has work, so an SM runs one code path and the instruction caches
+// hold one path (warps of different classes on one SM stalled on instruction
+// fetch); a warp whose class has finished moves on to the next class that has
+// not, so no SM idles while any class has work.  Group parameters are read
+// from the kernel's parameter space by group index (the MixArgs parameter is
+// __grid_constant__).  List entry e of a class is frame e - G.first of the
+// group G whose range holds it.
 
-template <class SYN>
-__global__ void __launch_bounds__(TPB, 6) k_product_mixed(const MixArgs m) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // the group table, copied into shared memory after the warps' areas, the
-  // remaining-mass area and its lock
-  MixGroup *tab = reinterpret_cast<MixGroup *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + TAIL_BYTES);
-  {
-    const int words = m.ngroups * (int)(sizeof(MixGroup) / 4);
-    const int *src = reinterpret_cast<const int *>(m.groups);
-    int *dst = reinterpret_cast<int *>(tab);
-    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
-  }
-  init_block_lock(smem, m.wstride, m.dpbytes, m.groups[0].P);
-  unsigned char *wsm = smem + warp * m.wstride;
-  const int64_t nslots = m.total * (int64_t)m.max_half;
-  unsigned long long *tslot = reinterpret_cast<unsigned long long *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16) + 2 * warp;
-  tally_clear(tslot, lane);
+// Decode words of class c until its list is done (returns 1) or the launch
+// stops on an error (returns 0).
+template <class SYN, int NPL>
+__device__ __noinline__ int mixed_class(const MixArgs &m, int c, unsigned char *smem, int warp, int lane) {
+  const MixClass &C = m.cls[c];
+  Scratch<NPL, SYN> sc;
+  bind_scratch(sc, smem, warp, m.wstride, m.dpbytes);
+  const int64_t nslots = C.total * (int64_t)m.max_half;
   for (;;) {
     int slot, w, f1;
-    if (!sched_take(m.ctrl, m.queue, nslots, m.total, m.slot_n, m.max_spin, lane, &slot, &w, &f1)) break;
-    const int64_t gf = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // the sign (the half's parity) is not needed here
-    int g = 0;
+    if (!sched_take(C.ctrl, m.err, C.queue, nslots, C.total, C.slot_n, m.max_spin, lane, &slot, &w, &f1)) {
+      int bad = 0;
+      if (lane == 0) bad = *reinterpret_cast<volatile int32_t *>(m.err);
+      return __shfl_sync(FULL, bad, 0) == 0;
+    }
+    const int64_t e = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // class list entry
+    int g = C.g0;
     if (lane == 0)
-      while (g + 1 < m.ngroups && m.groups[g + 1].first <= gf) g++;
+      while (g + 1 < C.g1 && m.groups[g + 1].first <= e) g++;
     g = __shfl_sync(FULL, g, 0);
-    const MixGroup &G = tab[g];
+    const MixGroup &G = m.groups[g];
     if (w >= G.code.n) continue;  // a ticket past this code's words
-    const int64_t li = gf - G.first;
-    const int64_t f = G.frames ? (int64_t)G.frames[li] : li;
+    const int64_t li = e - G.first;
+    int64_t f = G.frames ? (int64_t)G.frames[li] : li;
     int half = 0;
-    if (lane == 0) half = __ldcg(G.a.half_cur + f);
+    if (lane == 0) {
+      half = __ldcg(G.a.half_cur + f);
+      WordCtx *ctx = reinterpret_cast<WordCtx *>(sc.W());
+      ctx->li = e;
+      ctx->grp = g;
+    }
     half = __shfl_sync(FULL, half, 0);
-    const int npl = G.npl;
-    int q;
-    if (npl == 1)
-      q = mixed_word<SYN, 1>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane);
-    else if (npl == 2)
-      q = mixed_word<SYN, 2>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane);
-    else
-      q = mixed_word<SYN, 4>(G, smem, warp, m.wstride, m.dpbytes, f, w, half, lane);
-    if (lane == 0 && q < 0) atomicExch(G.a.bad + f, 1);
+    const int q = product_word<NPL, SYN, true, false, false>(G.code, G.P, G.a, sc, f, w, half, lane);
+    int64_t e2;
+    {
+      const volatile WordCtx *vc = reinterpret_cast<const volatile WordCtx *>(sc.W());
+      f = vc->f;
+      e2 = vc->li;
+      half = vc->half;
+      g = vc->grp;
+    }
+    const MixGroup &G2 = m.groups[g];
+    if (lane == 0 && q < 0) atomicExch(G2.a.bad + f, 1);
     __threadfence();  // release this word's L_E and hard decision
     __syncwarp();
     int done = 0;
-    if (lane == 0) done = atomicAdd(G.a.done_words + f, 1);
+    if (lane == 0) done = atomicAdd(G2.a.done_words + f, 1);
     done = __shfl_sync(FULL, done, 0);
-    if (done != G.code.n - 1) continue;
-    // the check uses this warp's word area as laid out for the group's NPL
-    if (npl == 1)
-      frame_after_half<1, false>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
-                          reinterpret_cast<uint64_t *>(wsm + Layout<1, SYN>::o_w), lane);
-    else if (npl == 2)
-      frame_after_half<2, false>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
-                          reinterpret_cast<uint64_t *>(wsm + Layout<2, SYN>::o_w), lane);
-    else
-      frame_after_half<4, false>(G.code, G.code, G.a, m.ctrl, m.queue, f, gf, half,
-                          reinterpret_cast<uint64_t *>(wsm + Layout<4, SYN>::o_w), lane);
+    if (done != G2.code.n - 1) continue;
+    frame_after_half<NPL, false>(G2.code, G2.code, G2.a, C.ctrl, C.queue, f, e2, half, sc.W(), lane);
+  }
+}
+
+template <class SYN, int MINB>
+__global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_constant__ MixArgs m) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  init_block_lock(smem, m.wstride, m.dpbytes, m.groups[0].P);
+  unsigned long long *tslot = reinterpret_cast<unsigned long long *>(smem + WARPS_PER_BLOCK * m.wstride + m.dpbytes + 16) + 2 * warp;
+  tally_clear(tslot, lane);
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  int c = m.home[smid % MIX_SM_TABLE];
+  unsigned done = 0;
+  const unsigned all = (1u << m.ncls) - 1u;
+  while (done != all) {
+    if ((done >> c) & 1u) {
+      c = c + 1 == m.ncls ? 0 : c + 1;
+      continue;
+    }
+    const int npl = m.cls[c].npl;
+    const int ok = npl == 1 ? mixed_class<SYN, 1>(m, c, smem, warp, lane)
+                            : (npl == 2 ? mixed_class<SYN, 2>(m, c, smem, warp, lane)
+                                        : mixed_class<SYN, 4>(m, c, smem, warp, lane));
+    if (!ok) break;
+    done |= 1u << c;
   }
   tally_flush(tslot, m.wsum, m.xf_count, lane);
 }
 
-// List and counters of the mixed form: every listed frame queued for its
-// current half.  Frames of groups marked `fresh` start at half 1 with cleared
-// counters; others resume where they were parked.  With per-frame half_stop
-// arrays, a frame parks after `epoch_halves` halves of this launch.
-static __global__ void k_mixed_init(const MixArgs m, int epoch_halves) {
-  const int64_t slots = m.total * (int64_t)m.max_half;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
-    if (i >= m.total) m.queue[i] = 0;
-    if (i < m.total) {
-      int g = 0;
-      while (g + 1 < m.ngroups && m.groups[g + 1].first <= i) g++;
+// Lists and counters of the mixed form: every listed frame queued in its
+// class's list for its current half.  Frames of groups marked `fresh` start
+// at half 1 with cleared counters; others resume where they were parked.
+// With per-frame half_stop arrays, a frame parks after `epoch_halves` halves
+// of this launch.
+static __global__ void k_mixed_init(const __grid_constant__ MixArgs m, int epoch_halves) {
+  for (int c = 0; c < m.ncls; c++) {
+    const MixClass &C = m.cls[c];
+    const int64_t slots = C.total * (int64_t)m.max_half;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
+      if (i >= C.total) {
+        C.queue[i] = 0;
+        continue;
+      }
+      int g = C.g0;
+      while (g + 1 < C.g1 && m.groups[g + 1].first <= i) g++;
       const MixGroup &G = m.groups[g];
       const int64_t li = i - G.first;
       const int64_t f = G.frames ? (int64_t)G.frames[li] : li;
@@ -692,15 +714,16 @@ static __global__ void k_mixed_init(const MixArgs m, int epoch_halves) {
       G.a.done_words[f] = 0;
       G.a.hmax[f] = 0;
       if (G.a.half_stop) G.a.half_stop[f] = G.a.half_cur[f] + epoch_halves - 1;
-      m.queue[i] = (G.a.half_cur[f] & 1) ? (int32_t)(i + 1) : -(int32_t)(i + 1);
+      C.queue[i] = (G.a.half_cur[f] & 1) ? (int32_t)(i + 1) : -(int32_t)(i + 1);
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      C.ctrl[0] = (int32_t)C.total;  // next slot to reserve
+      C.ctrl[1] = 0;                 // word tickets drawn
+      C.ctrl[2] = 0;                 // frames finished or parked
+      C.ctrl[3] = 0;
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    m.ctrl[0] = (int32_t)m.total;  // next slot to reserve
-    m.ctrl[1] = 0;                 // word tickets drawn
-    m.ctrl[2] = 0;                 // frames finished or parked
-    m.ctrl[3] = 0;                 // error
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *m.err = 0;
 }
 
 // list and counters of the persistent form: every frame queued for half 1
@@ -856,24 +879,24 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   return cudaGetLastError();
 }
 
-// Mixed form.  `m.groups` is device memory; `host_groups` the same table on
-// the host.  epoch_halves <= 0: no parking.
-template <class SYN>
-cudaError_t launch_product_mixed(const MixArgs &m, const MixGroup *host_groups, int epoch_halves, cudaStream_t s) {
-  if (m.total <= 0) return cudaSuccess;
-  k_mixed_init<<<(int)std::min<int64_t>((m.total * m.max_half + 255) / 256, 4096), 256, 0, s>>>(
+// Mixed form.  epoch_halves <= 0: no parking.
+template <class SYN, int MINB>
+cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_t s) {
+  int64_t slots = 0, words = 0;
+  for (int c = 0; c < m.ncls; c++) slots = std::max<int64_t>(slots, m.cls[c].total * m.max_half);
+  for (int g = 0; g < m.ngroups; g++) words += m.groups[g].count * m.groups[g].code.n;
+  if (words <= 0) return cudaSuccess;
+  k_mixed_init<<<(int)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, s>>>(
       m, epoch_halves > 0 ? epoch_halves : m.max_half);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int smem = WARPS_PER_BLOCK * m.wstride + m.dpbytes + TAIL_BYTES + m.ngroups * (int)sizeof(MixGroup);
-  auto kern = k_product_mixed<SYN>;
+  const int smem = WARPS_PER_BLOCK * m.wstride + m.dpbytes + TAIL_BYTES;
+  auto kern = k_product_mixed<SYN, MINB>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
   cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TPB, smem);
   if (occ < 1) occ = 1;
-  int64_t words = 0;
-  for (int g = 0; g < m.ngroups; g++) words += host_groups[g].count * host_groups[g].code.n;
   const int64_t want = (words + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)sm_count() * occ, want));
   kern<<<grid, TPB, smem, s>>>(m);

@@ -311,34 +311,48 @@ __device__ __forceinline__ void dp_unlock(int *lock, bool held, int lane) {
 // ----------------------------------------------------------------------------
 // warp helpers
 // ----------------------------------------------------------------------------
+// Bitonic sort of the warp's 32 * NPL keys, ascending (lane l holds keys
+// l, l + 32, ...).  The stages run as loops rather than unrolled: the sort is
+// straight-line work done once per word, and its unrolled form (about 20
+// stages of shuffles) made the kernel's code large enough that warps in other
+// phases of their words stalled on instruction fetch (measured 4-10% slower
+// for codes of 64 and 128 bits).
+// Compare-exchange of keys k and k ^ kj held by the same lane (stage distance
+// 32 kj); kj is one of the powers of two below NPL.
+template <int NPL>
+__device__ __forceinline__ void cmpx_regs(uint64_t (&v)[NPL], int kj, int size, int lane) {
+#pragma unroll
+  for (int k = 0; k < NPL; k++) {
+#pragma unroll
+    for (int c = 1; c < NPL; c <<= 1) {
+      if (c == kj && (k ^ c) > k) {
+        const int kp = k ^ c;
+        const bool asc = ((k * 32 + lane) & size) == 0;
+        uint64_t a = v[k], b = v[kp];
+        bool sw = asc ? (a > b) : (a < b);
+        v[k] = sw ? b : a;
+        v[kp] = sw ? a : b;
+      }
+    }
+  }
+}
 template <int NPL>
 __device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[NPL], int lane) {
   constexpr int N = 32 * NPL;
-#pragma unroll
+#pragma unroll 1
   for (int size = 2; size <= N; size <<= 1) {
+    if (NPL > 1) {
+#pragma unroll 1
+      for (int j = size >> 1; j >= 32; j >>= 1) cmpx_regs<NPL>(v, j >> 5, size, lane);
+    }
+#pragma unroll 1
+    for (int j = min(size >> 1, 16); j > 0; j >>= 1) {
 #pragma unroll
-    for (int j = size >> 1; j > 0; j >>= 1) {
-      if (j >= 32) {
-        const int kj = j >> 5;
-#pragma unroll
-        for (int k = 0; k < NPL; k++) {
-          const int kp = k ^ kj;
-          if (kp > k) {
-            const bool asc = ((k * 32 + lane) & size) == 0;
-            uint64_t a = v[k], b = v[kp];
-            bool sw = asc ? (a > b) : (a < b);
-            v[k] = sw ? b : a;
-            v[kp] = sw ? a : b;
-          }
-        }
-      } else {
-#pragma unroll
-        for (int k = 0; k < NPL; k++) {
-          uint64_t o = __shfl_xor_sync(FULL, v[k], j);
-          const bool asc = ((k * 32 + lane) & size) == 0;
-          const bool lower = (lane & j) == 0;
-          v[k] = (lower == asc) ? (v[k] < o ? v[k] : o) : (v[k] < o ? o : v[k]);
-        }
+      for (int k = 0; k < NPL; k++) {
+        uint64_t o = __shfl_xor_sync(FULL, v[k], j);
+        const bool asc = ((k * 32 + lane) & size) == 0;
+        const bool lower = (lane & j) == 0;
+        v[k] = (lower == asc) ? (v[k] < o ? v[k] : o) : (v[k] < o ? o : v[k]);
       }
     }
   }
@@ -837,14 +851,15 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
     const float tqf = tq.h + tq.l;
     const float r = enz - tqf;
     const bool in_range = enz > 0x1p-60f && enz < 0x1p60f;
-    if (in_range && r > 0.02f * (enz + tqf)) return log2f(r);
+    // the hardware log2 (about 2^-22 relative): far inside the soft output's tolerance
+    if (in_range && r > 0.02f * (enz + tqf)) return __log2f(r);
     if (in_range) {
       const DF E = class_total_df<NPL, SYN>(sc, n, cls, lane);
       const DF R = df_add(E, DF{-tq.h, -tq.l});
 #ifdef SG_PHASE_PROFILE
       if (lane == 0) SG_PROF(R.h > 0x1p-26f * (E.h + tq.h) ? 12 : 13, 1);
 #endif
-      if (R.h > 0x1p-26f * (E.h + tq.h)) return log2f(R.h + R.l);
+      if (R.h > 0x1p-26f * (E.h + tq.h)) return __log2f(R.h + R.l);
     }
 #ifdef SG_PHASE_PROFILE
     if (!in_range && lane == 0) SG_PROF(15, 1);
@@ -1165,36 +1180,50 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     res.pmiss = 1.f;
     res.logD = M;
   } else {
-    // log(R phi + sum_l p_l), all relative to p(0): max plus log of a sum
+    // log(R phi + sum_l p_l), all relative to p(0): max plus log of a sum.
+    // The hardware exponential and logarithm (relative errors near 2^-21 over
+    // these ranges) keep L_APP within about 1e-5 of the exact formula, far
+    // inside the soft output's tolerance; no decision is taken on them.
     float mx = M;
     for (int l = 0; l < nhit; l++) mx = fmaxf(mx, sc.lp()[l]);
-    float sum = M == -CUDART_INF_F ? 0.f : expf(M - mx);
-    for (int l = 0; l < nhit; l++) sum += expf(sc.lp()[l] - mx);
-    const float D = mx + logf(sum);
+    float sum = M == -CUDART_INF_F ? 0.f : __expf(M - mx);
+    for (int l = 0; l < nhit; l++) sum += __expf(sc.lp()[l] - mx);
+    const float D = mx + __logf(sum);
     res.logD = D;
-    const float pm = M == -CUDART_INF_F ? 0.f : expf(M - D);
+    const float pm = M == -CUDART_INF_F ? 0.f : __expf(M - D);
     res.pmiss = pm;
     // APP of each listed word (list weights relative to the normaliser)
-    if (lane < nhit) sc.wl()[lane] = expf(sc.lp()[lane] - D);
+    if (lane < nhit) sc.wl()[lane] = __expf(sc.lp()[lane] - D);
     __syncwarp();
+    // eq. LLRi: the miss term, then each listed word adds its APP to the side
+    // of its bit; a list word's bit mask is read once for all the lane's bits
+    float a0[NPL], a1[NPL];
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
-      const int i = lane + 32 * k;
-      const float x = sc.lam_at(i);
+      const float x = sc.lam_at(lane + 32 * k);
       // sigma(x) and sigma(-x) without cancellation
-      const float ex = expf(-fabsf(x));
-      const float sp = __frcp_rn(1.f + ex), sn = ex * sp;  // sigma(|x|), sigma(-|x|)
-      float a0 = pm * (x >= 0.f ? sp : sn);              // miss term, bit 0
-      float a1 = pm * (x >= 0.f ? sn : sp);              // miss term, bit 1
-      const uint64_t bitm = 1ull << (i & 63);
-      for (int l = 0; l < nhit; l++) {
-        if (sc.cw()[l * NM + (i >> 6)] & bitm)
-          a1 += sc.wl()[l];
+      const float ex = __expf(-fabsf(x));
+      const float sp = __fdividef(1.f, 1.f + ex), sn = ex * sp;  // sigma(|x|), sigma(-|x|)
+      a0[k] = pm * (x >= 0.f ? sp : sn);                          // miss term, bit 0
+      a1[k] = pm * (x >= 0.f ? sn : sp);                          // miss term, bit 1
+    }
+    for (int l = 0; l < nhit; l++) {
+      const float wlv = sc.wl()[l];
+#pragma unroll
+      for (int k = 0; k < NPL; k++) {
+        const int i = lane + 32 * k;
+        if ((sc.cw()[l * NM + (i >> 6)] >> (i & 63)) & 1ull)
+          a1[k] += wlv;
         else
-          a0 += sc.wl()[l];
+          a0[k] += wlv;
       }
-      // both sums lie in (1e-30, 1 + 1e-6]: __fdividef's range, 2 ulp
-      lapp[k] = (a0 > 1e-30f && a1 > 1e-30f) ? logf(__fdividef(a0, a1)) : lapp_logdomain<NPL, SYN>(sc, nhit, M, x, i);
+    }
+#pragma unroll
+    for (int k = 0; k < NPL; k++) {
+      // both sums lie in (1e-30, 1 + 1e-6]: __fdividef's range
+      lapp[k] = (a0[k] > 1e-30f && a1[k] > 1e-30f)
+                    ? __logf(__fdividef(a0[k], a1[k]))
+                    : lapp_logdomain<NPL, SYN>(sc, nhit, M, sc.lam_at(lane + 32 * k), lane + 32 * k);
     }
   }
 #ifdef SG_PHASE_PROFILE

@@ -197,16 +197,18 @@ def test_host_entry_equals_device_entry(env, F, pinned):
 
 def test_mixed_form_equals_each_code_alone(env):
     """Frames of eBCH(32,26)^2, (64,51)^2 and (128,120)^2 in 4:2:1 proportion,
-    Eb/N0 uniform in 2.5..4 dB per frame, decoded by one mixed launch, give
-    exactly what product_decode_persistent gives for each code alone."""
+    Eb/N0 uniform in 2.5..4 dB per frame, plus eBCH(64,57)^2 frames (a second
+    code of the (64,51) lane layout, so one class holds two codes), decoded by
+    one mixed launch, give exactly what product_decode_persistent gives for
+    each code alone.  The groups are passed out of class order."""
     torch, sg = env
     rng = np.random.default_rng(77)
-    specs = [("ebch_32_26", 48), ("ebch_64_51", 24), ("ebch_128_120", 12)]
+    specs = [("ebch_64_51", 24), ("ebch_32_26", 48), ("ebch_128_120", 12), ("ebch_64_57", 20)]
     groups, refs, codes = [], [], []
     for i, (name, F) in enumerate(specs):
         code = ebch(name)
         U, X, lch = awgn_frames(code, F, rng.uniform(2.5, 4.0, F), seed=800 + i)
-        if i == 1:
+        if i == 0:
             lch[5, 0, 0] = np.nan
         c = sg.Code.from_linear_code(code)
         d = torch.from_numpy(lch).cuda()
@@ -220,7 +222,7 @@ def test_mixed_form_equals_each_code_alone(env):
     for (name, F), o, r in zip(specs, outs, refs):
         for key in ("bits", "half_iters", "status", "queries"):
             np.testing.assert_array_equal(o[key].cpu().numpy(), r[key], err_msg=f"{name} {key}")
-    assert outs[1]["status"][5].item() == 2
+    assert outs[0]["status"][5].item() == 2
     assert info["launches"] == 2 and info["timing_ms"] > 0
     # groups needing 32-bit and 64-bit syndromes cannot share a launch
     H = np.random.default_rng(5).integers(0, 2, (40, 64)).astype(np.uint8)
