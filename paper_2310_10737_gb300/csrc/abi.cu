@@ -402,6 +402,9 @@ cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P
 }
 sg::SisoParams siso_params_of(int L, int64_t cap, float thr) { return siso_params(L, cap, thr); }
 int32_t queue_wait_us() { return (int32_t)g_queue_wait_us.load(); }
+int dp_slice(const sogrand_code *c) {
+  return sg::dp_slice_bytes(c->n <= 32 ? 1 : (c->n <= 64 ? 2 : 4), c->m > 32 ? 8 : 4, c->jmax);
+}
 int sm_count_of_device() {
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
@@ -420,6 +423,9 @@ int dp_area_bytes(int npl, int syn_bytes, int jmax) {
   if (npl == 1) return syn_bytes == 4 ? Layout<1, uint32_t>::dp_bytes(jmax) : Layout<1, uint64_t>::dp_bytes(jmax);
   if (npl == 2) return syn_bytes == 4 ? Layout<2, uint32_t>::dp_bytes(jmax) : Layout<2, uint64_t>::dp_bytes(jmax);
   return syn_bytes == 4 ? Layout<4, uint32_t>::dp_bytes(jmax) : Layout<4, uint64_t>::dp_bytes(jmax);
+}
+int dp_slice_bytes(int npl, int syn_bytes, int jmax) {
+  return (dp_area_bytes(npl, syn_bytes, jmax) + TAIL_BYTES + 127) & ~127;
 }
 }  // namespace sg
 
@@ -716,6 +722,17 @@ size_t persistent_scratch_bytes(int64_t F, int nr, int nc, int nm, int max_iter)
          al256(4 * sizeof(int32_t));
 }
 
+// The global remaining-mass region of a persistent launch: one slice per
+// resident block (at most 8 blocks per SM in either schedule).
+constexpr int MAX_BLOCKS_PER_SM = 8;
+inline int npl_of_n(int n) { return n <= 32 ? 1 : (n <= 64 ? 2 : 4); }
+int dp_slice_of(const sogrand_code *rc, const sogrand_code *cc) {
+  return sg::dp_slice_bytes(npl_of_n(rc->n), rc->m > 32 ? 8 : 4, std::max(rc->jmax, cc->jmax));
+}
+size_t dp_region_bytes(const sogrand_code *rc, const sogrand_code *cc) {
+  return al256((size_t)sgi::sm_count_of_device() * MAX_BLOCKS_PER_SM * dp_slice_of(rc, cc));
+}
+
 // Queue set-up and the persistent kernel for F frames on stream s (nothing
 // is waited for).  Outputs that are null go to the scratch.  *err_dev is the
 // device word that holds the kernel's timeout flag afterwards.
@@ -758,6 +775,10 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   a.par_queries = par_queries ? par_queries : pq_s;
   a.status = status ? status : st_s;
   a.max_spin = (int32_t)g_queue_wait_us.load();  // back-off without any work before giving up
+  // the blocks' remaining-mass areas: the region that follows the scratch
+  a.dp_area = (unsigned char *)(mem + al256(persistent_scratch_bytes(F, nr, nc, nm, max_iter)));
+  a.dp_stride = dp_slice_of(c, cc);
+  a.dp_blocks = sgi::sm_count_of_device() * MAX_BLOCKS_PER_SM;
   a.xf_count = xf;
   a.wsum = wsum;
   *err_dev = a.ctrl + 3;
@@ -792,7 +813,8 @@ int persistent_decode(sogrand_code *rc_, const sogrand_code *cc_, int diag, int6
   if (rc != SOGRAND_OK) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   char *mem = nullptr;
-  if (scratch_alloc(&mem, persistent_scratch_bytes(F, c->n, cc->n, c->nm, max_iter), s) != cudaSuccess)
+  if (scratch_alloc(&mem, al256(persistent_scratch_bytes(F, c->n, cc->n, c->nm, max_iter)) + dp_region_bytes(c, cc), s) !=
+      cudaSuccess)
     return SOGRAND_ENOMEM;
   const sg::SisoParams P = siso_params(L, cap, thr);
   const bool timed = stats && stats->timing_ms;
@@ -911,7 +933,7 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   const int64_t chunk = (F + K - 1) / K;
   const size_t b_in = al256((size_t)F * in_f), b_bits = al256((size_t)F * nb);
   const size_t b_out = b_in + b_bits + al256((size_t)F * 4) + al256((size_t)F) + al256((size_t)F * 8);
-  const size_t b_scr = al256(persistent_scratch_bytes(chunk, nr, nc, nm, max_iter));
+  const size_t b_scr = al256(persistent_scratch_bytes(chunk, nr, nc, nm, max_iter)) + dp_region_bytes(c, cc);
   char *mem = nullptr;
   if (scratch_alloc(&mem, b_out + 2 * b_scr + 256, s) != cudaSuccess) return SOGRAND_ENOMEM;
   float *d_in = (float *)mem;
@@ -1053,6 +1075,15 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   }
   const size_t o_err = bytes;
   bytes += 256;
+  // the blocks' remaining-mass areas, one slice per resident block
+  int slice = 0;
+  for (int x = 0; x < ng; x++) {
+    const sogrand_code *c = groups[order[x]].code;
+    slice = std::max(slice, sg::dp_slice_bytes(npl_of(c->n), syn64 ? 8 : 4, c->jmax));
+  }
+  const size_t o_dp = bytes;
+  const int dp_blocks = sgi::sm_count_of_device() * MAX_BLOCKS_PER_SM;
+  bytes += al256((size_t)dp_blocks * slice);
   char *mem = nullptr;
   if (scratch_alloc(&mem, bytes, s) != cudaSuccess) return SOGRAND_ENOMEM;
   for (int c = 0; c < ncls; c++) {
@@ -1113,6 +1144,9 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   m.dpbytes = dpbytes;
   m.max_spin = (int32_t)g_queue_wait_us.load();
   m.err = gctrl + 3;
+  m.dp_area = (unsigned char *)(mem + o_dp);
+  m.dp_stride = slice;
+  m.dp_blocks = dp_blocks;
   m.xf_count = stats ? stats->xf_words : nullptr;
   m.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
   // home classes: SM ids spread over the classes in proportion to their

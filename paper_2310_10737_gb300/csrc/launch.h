@@ -65,6 +65,11 @@ struct ProductArgs {
   int32_t grid_cap;           // > 0: at most this many blocks
   // plain form only: query count of every word of the current half, [F][hbw] (or null)
   int32_t *wq;
+  // persistent form: the blocks' remaining-mass areas in global memory (block
+  // b uses dp_area + b * dp_stride: the area, its lock word and the warps'
+  // tally slots), for at most dp_blocks blocks; null: in shared memory
+  unsigned char *dp_area;
+  int32_t dp_stride, dp_blocks;
 };
 
 // Mixed form: groups of frames, one code per group, in one launch.  The
@@ -105,6 +110,8 @@ struct MixArgs {
   int32_t dpbytes;         // the block's remaining-mass area: the largest of the groups
   int32_t max_spin;
   int32_t *err;            // [1] launch-wide error word (a group's a.ctrl + 3)
+  unsigned char *dp_area;  // the blocks' remaining-mass areas in global memory (as ProductArgs)
+  int32_t dp_stride, dp_blocks;
   int32_t *xf_count;
   unsigned long long *wsum;
   uint8_t home[MIX_SM_TABLE];  // class whose code path the warps of SM s run first
@@ -143,5 +150,7 @@ cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_
 // shared-memory layout sizes of a code: per warp, and the block's remaining-mass area
 int warp_area_bytes(int npl, int syn_bytes);
 int dp_area_bytes(int npl, int syn_bytes, int jmax);
+// bytes of one block's slice of a global remaining-mass region (area, lock, tallies)
+int dp_slice_bytes(int npl, int syn_bytes, int jmax);
 
 }  // namespace sg

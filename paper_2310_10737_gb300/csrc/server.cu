@@ -43,6 +43,7 @@ cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P
 int sm_count_of_device();
 sg::SisoParams siso_params_of(int L, int64_t cap, float thr);
 int32_t queue_wait_us();
+int dp_slice(const sogrand_code *c);
 }  // namespace sgi
 
 namespace {
@@ -78,6 +79,8 @@ struct Pool {
   uint8_t *bits = nullptr, *status = nullptr;
   int32_t *half_iters = nullptr, *hmax = nullptr, *half_cur = nullptr, *done_words = nullptr, *bad = nullptr;
   int32_t *half_stop = nullptr, *queue = nullptr, *ctrl = nullptr, *list = nullptr;
+  unsigned char *dp_area = nullptr;  // the launch blocks' remaining-mass areas
+  int dp_stride = 0, dp_blocks = 0;
   int64_t *queries = nullptr, *par_queries = nullptr;
   int32_t *h_list = nullptr;   // pinned [slots]
   uint8_t *h_status = nullptr; // pinned [slots]
@@ -174,6 +177,7 @@ size_t carve(Pool &p, int max_iter, char *mem) {
   p.par_queries = (int64_t *)take(S * 8);
   p.queue = (int32_t *)take(S * 2 * max_iter * 4);
   p.ctrl = (int32_t *)take(16);
+  p.dp_area = (unsigned char *)take((size_t)p.dp_blocks * p.dp_stride);
   return off;
 }
 
@@ -313,6 +317,9 @@ cudaError_t launch(sogrand_server *sv, Pool &p, int64_t total_words) {
   a.bad = p.bad;
   a.ctrl = p.ctrl;
   a.max_spin = sgi::queue_wait_us();
+  a.dp_area = p.dp_area;
+  a.dp_stride = p.dp_stride;
+  a.dp_blocks = p.dp_blocks;
   a.half_stop = p.half_stop;
   a.frame_list = p.list;
   a.epoch_halves = sv->epoch_halves;
@@ -418,6 +425,8 @@ int sogrand_server_create(int n_codes, sogrand_code *const *codes, const int64_t
     p->n = sgi::code_n(codes[i]);
     p->nm = sgi::code_nm(codes[i]);
     p->slots = slots[i];
+    p->dp_stride = sgi::dp_slice(codes[i]);
+    p->dp_blocks = sgi::sm_count_of_device() * 8;  // a slice for every block a launch can have resident
     const size_t bytes = carve(*p, max_iter, nullptr);
     if (cudaMalloc(&p->mem, bytes) != cudaSuccess) {
       rc = SOGRAND_ENOMEM;

@@ -1112,8 +1112,6 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
 #endif
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
     if (lane < lim) e = __ldg(O.ent + tb + q + lane);
-    // the next chunk's entries into L1 while this one is tested (within the stored entries)
-    if (q + 32 + lane < qlim) asm volatile("prefetch.global.L1 [%0];" ::"l"(O.ent + tb + q + 32 + lane));
     const int w = e.x & 0xff;
     const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
     DF mass;
