@@ -424,9 +424,7 @@ int dp_area_bytes(int npl, int syn_bytes, int jmax) {
   if (npl == 2) return syn_bytes == 4 ? Layout<2, uint32_t>::dp_bytes(jmax) : Layout<2, uint64_t>::dp_bytes(jmax);
   return syn_bytes == 4 ? Layout<4, uint32_t>::dp_bytes(jmax) : Layout<4, uint64_t>::dp_bytes(jmax);
 }
-int dp_slice_bytes(int npl, int syn_bytes, int jmax) {
-  return (dp_area_bytes(npl, syn_bytes, jmax) + TAIL_BYTES + 127) & ~127;
-}
+int dp_slice_bytes(int npl, int syn_bytes, int jmax) { return (dp_area_bytes(npl, syn_bytes, jmax) + 127) & ~127; }
 }  // namespace sg
 
 extern "C" {

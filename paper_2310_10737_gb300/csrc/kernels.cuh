@@ -27,32 +27,35 @@ __host__ __device__ inline int block_scratch_bytes(int jmax) {
   return Layout<NPL, SYN>::block_bytes(jmax);
 }
 
-// The block's remaining-mass area, followed by its lock word and the warps'
-// tally slots: in shared memory after the warps' areas (`wstride` bytes
-// each), or the block's own slice of a global region when the launch passes
-// one.  The area serves about 1% of component decodings or fewer; in global
-// memory it leaves the SM's on-chip memory to L1, which holds the hot
-// query-order entries (a block of a long code kept 14 KB of shared memory for
-// it).
+// The block's tail (lock word of its remaining-mass area and the warps'
+// tally slots) in shared memory after the warps' areas (`wstride` bytes
+// each); the remaining-mass area after the tail, or the block's own slice of
+// a global region when the launch passes one.  The area serves about 1% of
+// component decodings or fewer; in global memory it leaves the SM's on-chip
+// memory to L1, which holds the hot query-order entries (a block of a long
+// code kept 14 KB of shared memory for it).
+__device__ __forceinline__ unsigned char *block_tail(unsigned char *smem, int wstride) {
+  return smem + WARPS_PER_BLOCK * wstride;
+}
 __device__ __forceinline__ unsigned char *block_dp_area(unsigned char *smem, int wstride, unsigned char *dp_global,
                                                         int dp_stride) {
-  return dp_global ? dp_global + (size_t)blockIdx.x * dp_stride : smem + WARPS_PER_BLOCK * wstride;
+  return dp_global ? dp_global + (size_t)blockIdx.x * dp_stride : block_tail(smem, wstride) + TAIL_BYTES;
 }
 
-// Bind warp `warp`'s view: its area in shared memory (`wstride` bytes a warp)
-// and the block's remaining-mass area `dpb` of `dpbytes`.
+// Bind warp `warp`'s view: its area in shared memory (`wstride` bytes a warp),
+// the block's remaining-mass area `dpb` and tail `tl`.
 template <int NPL, class SYN>
 __device__ __forceinline__ void bind_scratch(Scratch<NPL, SYN> &sc, unsigned char *smem, int warp, int wstride,
-                                             unsigned char *dpb, int dpbytes) {
-  sc.bind(smem + warp * wstride, dpb, dpbytes);
+                                             unsigned char *dpb, unsigned char *tl) {
+  sc.bind(smem + warp * wstride, dpb, tl);
 }
 
 // Clear the block's remaining-mass lock and store its poll limit (every
 // thread of the block calls this).  P.lock_preheld starts the block with the
 // lock taken, as if a warp held it and never released it.
-__device__ __forceinline__ void init_block_lock(unsigned char *dpb, int dpbytes, const SisoParams &P) {
+__device__ __forceinline__ void init_block_lock(unsigned char *tl, const SisoParams &P) {
   if (threadIdx.x == 0) {
-    int *lock = reinterpret_cast<int *>(dpb + dpbytes);
+    int *lock = reinterpret_cast<int *>(tl);
     lock[0] = P.lock_preheld ? 1 : 0;
     lock[1] = P.lock_polls;
   }
@@ -66,10 +69,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const 
   using LY = Layout<NPL, SYN>;
   constexpr int NM = (32 * NPL + 63) / 64;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char *dpb = smem + WARPS_PER_BLOCK * LY::warp_bytes;
-  init_block_lock(dpb, LY::dp_bytes(code.jmax), P);
+  unsigned char *tl = block_tail(smem, LY::warp_bytes);
+  init_block_lock(tl, P);
   Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, LY::warp_bytes, dpb, LY::dp_bytes(code.jmax));
+  bind_scratch(sc, smem, warp, LY::warp_bytes, tl + TAIL_BYTES, tl);
   const int n = code.n;
   const int64_t nwarps = (int64_t)gridDim.x * WARPS_PER_BLOCK;
   for (int64_t w = (int64_t)blockIdx.x * WARPS_PER_BLOCK + warp; w < a.n_words; w += nwarps) {
@@ -125,10 +128,10 @@ __global__ void k_trace(const DevCode code, const float *lam_in, int max_q, uint
   extern __shared__ __align__(16) unsigned char smem[];
   using LY = Layout<NPL, SYN>;
   const int lane = threadIdx.x & 31;
-  unsigned char *dpb = smem + WARPS_PER_BLOCK * LY::warp_bytes;
-  init_block_lock(dpb, LY::dp_bytes(code.jmax), SisoParams{1, 1, 0.f});
+  unsigned char *tl = block_tail(smem, LY::warp_bytes);
+  init_block_lock(tl, SisoParams{1, 1, 0.f});
   Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, 0, LY::warp_bytes, dpb, LY::dp_bytes(code.jmax));
+  bind_scratch(sc, smem, 0, LY::warp_bytes, tl + TAIL_BYTES, tl);
   float lam[NPL];
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
@@ -390,10 +393,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode rowc, 
   using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int jm = max(rowc.jmax, colc.jmax);
-  unsigned char *dpb = smem + WARPS_PER_BLOCK * LY::warp_bytes;
-  init_block_lock(dpb, LY::dp_bytes(jm), P);
+  unsigned char *tl = block_tail(smem, LY::warp_bytes);
+  init_block_lock(tl, P);
   Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, LY::warp_bytes, dpb, LY::dp_bytes(jm));
+  bind_scratch(sc, smem, warp, LY::warp_bytes, tl + TAIL_BYTES, tl);
   const DevCode &code = ROWS ? rowc : colc;  // the code of this half's words
   const int n = ROWS ? a.nc : a.nr;          // words per frame in this half
   const int64_t items = a.n_frames * n;
@@ -568,10 +571,10 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
   using LY = Layout<NPL, SYN>;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int jm = max(rowc.jmax, colc.jmax);
-  unsigned char *dpb = block_dp_area(smem, LY::warp_bytes, a.dp_area, a.dp_stride);
-  init_block_lock(dpb, LY::dp_bytes(jm), P);
+  unsigned char *tl = block_tail(smem, LY::warp_bytes);
+  init_block_lock(tl, P);
   Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, LY::warp_bytes, dpb, LY::dp_bytes(jm));
+  bind_scratch(sc, smem, warp, LY::warp_bytes, block_dp_area(smem, LY::warp_bytes, a.dp_area, a.dp_stride), tl);
   const int slot_n = GEN ? max(a.nr, a.nc) : rowc.n;  // tickets per list slot: the most words in a half
   const int64_t nslots = a.n_frames * (int64_t)a.max_half;  // a frame has at most max_half halves
   tally_clear(sc.tally(), lane);
@@ -625,11 +628,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
 // Decode words of class c until its list is done (returns 1) or the launch
 // stops on an error (returns 0).
 template <class SYN, int NPL>
-__device__ __noinline__ int mixed_class(const MixArgs &m, int c, unsigned char *smem, unsigned char *dpb, int warp,
-                                        int lane) {
+__device__ __noinline__ int mixed_class(const MixArgs &m, int c, unsigned char *smem, unsigned char *dpb,
+                                        unsigned char *tl, int warp, int lane) {
   const MixClass &C = m.cls[c];
   Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, m.wstride, dpb, m.dpbytes);
+  bind_scratch(sc, smem, warp, m.wstride, dpb, tl);
   const int64_t nslots = C.total * (int64_t)m.max_half;
   for (;;) {
     int slot, w, f1;
@@ -680,9 +683,10 @@ template <class SYN, int MINB>
 __global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_constant__ MixArgs m) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  unsigned char *tl = block_tail(smem, m.wstride);
   unsigned char *dpb = block_dp_area(smem, m.wstride, m.dp_area, m.dp_stride);
-  init_block_lock(dpb, m.dpbytes, m.groups[0].P);
-  unsigned long long *tslot = reinterpret_cast<unsigned long long *>(dpb + m.dpbytes + 16) + 2 * warp;
+  init_block_lock(tl, m.groups[0].P);
+  unsigned long long *tslot = reinterpret_cast<unsigned long long *>(tl + 16) + 2 * warp;
   tally_clear(tslot, lane);
   unsigned smid;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
@@ -695,9 +699,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_consta
       continue;
     }
     const int npl = m.cls[c].npl;
-    const int ok = npl == 1 ? mixed_class<SYN, 1>(m, c, smem, dpb, warp, lane)
-                            : (npl == 2 ? mixed_class<SYN, 2>(m, c, smem, dpb, warp, lane)
-                                        : mixed_class<SYN, 4>(m, c, smem, dpb, warp, lane));
+    const int ok = npl == 1 ? mixed_class<SYN, 1>(m, c, smem, dpb, tl, warp, lane)
+                            : (npl == 2 ? mixed_class<SYN, 2>(m, c, smem, dpb, tl, warp, lane)
+                                        : mixed_class<SYN, 4>(m, c, smem, dpb, tl, warp, lane));
     if (!ok) break;
     done |= 1u << c;
   }
@@ -882,7 +886,7 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   // with a global remaining-mass region only the warps' areas are shared memory
-  const int smem = a.dp_area ? WARPS_PER_BLOCK * Layout<NPL, SYN>::warp_bytes
+  const int smem = a.dp_area ? WARPS_PER_BLOCK * Layout<NPL, SYN>::warp_bytes + TAIL_BYTES
                              : block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
   auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8, GEN> : k_product_persistent<NPL, SYN, 6, GEN>;
   e = set_smem(kern, smem);
@@ -911,7 +915,7 @@ cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_
       m, epoch_halves > 0 ? epoch_halves : m.max_half);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const int smem = m.dp_area ? WARPS_PER_BLOCK * m.wstride : WARPS_PER_BLOCK * m.wstride + m.dpbytes + TAIL_BYTES;
+  const int smem = WARPS_PER_BLOCK * m.wstride + TAIL_BYTES + (m.dp_area ? 0 : m.dpbytes);
   auto kern = k_product_mixed<SYN, MINB>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;

@@ -66,8 +66,8 @@ struct ProductArgs {
   // plain form only: query count of every word of the current half, [F][hbw] (or null)
   int32_t *wq;
   // persistent form: the blocks' remaining-mass areas in global memory (block
-  // b uses dp_area + b * dp_stride: the area, its lock word and the warps'
-  // tally slots), for at most dp_blocks blocks; null: in shared memory
+  // b uses dp_area + b * dp_stride), for at most dp_blocks blocks; null: in
+  // shared memory
   unsigned char *dp_area;
   int32_t dp_stride, dp_blocks;
 };
@@ -150,7 +150,7 @@ cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_
 // shared-memory layout sizes of a code: per warp, and the block's remaining-mass area
 int warp_area_bytes(int npl, int syn_bytes);
 int dp_area_bytes(int npl, int syn_bytes, int jmax);
-// bytes of one block's slice of a global remaining-mass region (area, lock, tallies)
+// bytes of one block's slice of a global remaining-mass region
 int dp_slice_bytes(int npl, int syn_bytes, int jmax);
 
 }  // namespace sg

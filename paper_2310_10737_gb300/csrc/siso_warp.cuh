@@ -210,13 +210,13 @@ struct RankRec {
   float t;
 };
 
-// Shared memory of a block: one area per warp (below), then one
-// remaining-mass area for the whole block (the cost DP, needed by about 0.2%
-// of component decodings), then a tail: the area's lock word (16 bytes) and
-// one 16-byte tally slot per warp (summed pattern weights, extended-range
-// words), flushed to global counters when the warp exits.
-// lock word (and, after it, the lock's poll limit) + one tally slot per warp,
-// after the block's remaining-mass area
+// Shared memory of a block: one area per warp (below), then a tail: the lock
+// word of the block's remaining-mass area with the lock's poll limit (16
+// bytes) and one 16-byte tally slot per warp (summed pattern weights,
+// extended-range words), flushed to global counters when the warp exits; then
+// (unless the launch puts it in global memory) the remaining-mass area for the
+// whole block (the cost DP, needed by about 1% of component decodings or
+// fewer).
 constexpr int TAIL_BYTES = 16 + 16 * WARPS_PER_BLOCK;
 
 template <int NPL, class SYN>
@@ -236,27 +236,28 @@ struct Layout {
   // (A separate area would cost 1 KB per block, which moved the shared-memory
   // carveout of the 8-block schedule up a step and shrank L1 by a quarter.)
   static constexpr int o_lam = o_w + 32;
-  static_assert(32 + 4 * NT <= 8 * NT * NM, "lambda fits in the frame-check area");
+  static_assert(32 + 4 * NT + 4 * (NPL + 1) <= 8 * NT * NM, "lambda and the word head fit in the frame-check area");
   static constexpr int warp_bytes = align16(o_w + 8 * NT * NM);
   // block area (sized for the 8-byte XF policy): sfac[NT+1], fu[NT+1], fb[NT+1], ek[J] (float), he[J], ho[J]
   static __host__ __device__ int dp_bytes(int jm) { return align16(24 * (NT + 1) + 20 * jm + 32); }
-  // a block of WARPS_PER_BLOCK warps: their areas, the remaining-mass area and the tail
-  static __host__ __device__ int block_bytes(int jm) { return WARPS_PER_BLOCK * warp_bytes + dp_bytes(jm) + TAIL_BYTES; }
+  // a block of WARPS_PER_BLOCK warps: their areas, the tail and the remaining-mass area
+  static __host__ __device__ int block_bytes(int jm) { return WARPS_PER_BLOCK * warp_bytes + TAIL_BYTES + dp_bytes(jm); }
 };
 
-// A warp's view of the block's shared memory: its own area and the block's
-// remaining-mass area with its lock word.  Only the two base addresses are
-// kept; every array is a fixed offset from them.
+// A warp's view of the block's scratch: its own area, the block's tail
+// (lock word and tally slots, shared memory) and the block's remaining-mass
+// area (shared or global memory).  Only the base addresses are kept; every
+// array is a fixed offset from them.
 template <int NPL, class SYN>
 struct Scratch {
   using LY = Layout<NPL, SYN>;
   unsigned char *base;  // this warp's area
-  unsigned char *dp;    // the block's remaining-mass area, followed by its lock word
-  int dpbytes;
-  __device__ void bind(unsigned char *warp_area, unsigned char *dp_area, int dp_bytes) {
+  unsigned char *dp;    // the block's remaining-mass area
+  unsigned char *tl;    // the block's tail: lock word and poll limit, then the warps' tally slots
+  __device__ void bind(unsigned char *warp_area, unsigned char *dp_area, unsigned char *tail_area) {
     base = warp_area;
     dp = dp_area;
-    dpbytes = dp_bytes;
+    tl = tail_area;
   }
   __device__ float *l2() const { return reinterpret_cast<float *>(base + LY::o_l2); }
   __device__ float *al() const { return reinterpret_cast<float *>(base + LY::o_al); }
@@ -270,11 +271,14 @@ struct Scratch {
   // the soft output, so that it holds no registers while the search runs
   __device__ float *lamv() const { return reinterpret_cast<float *>(base + LY::o_lam); }
   __device__ float lam_at(int i) const { return *reinterpret_cast<const volatile float *>(base + LY::o_lam + 4 * i); }
+  // the word's hard decision words (NPL) and 1-line parameter, after lambda
+  __device__ unsigned *headv() const { return reinterpret_cast<unsigned *>(base + LY::o_lam + 4 * LY::NT); }
+  __device__ unsigned head_at(int k) const { return *reinterpret_cast<const volatile unsigned *>(base + LY::o_lam + 4 * LY::NT + 4 * k); }
   __device__ unsigned char *tail() const { return dp; }
-  __device__ int *lock() const { return reinterpret_cast<int *>(dp + dpbytes); }
+  __device__ int *lock() const { return reinterpret_cast<int *>(tl); }
   // this warp's tally slot: [0] summed pattern weights, [1] extended-range words
   __device__ unsigned long long *tally() const {
-    return reinterpret_cast<unsigned long long *>(dp + dpbytes + 16) + 2 * (threadIdx.x >> 5);
+    return reinterpret_cast<unsigned long long *>(tl + 16) + 2 * (threadIdx.x >> 5);
   }
 };
 
@@ -1022,7 +1026,7 @@ __device__ __forceinline__ void record_hit(const Scratch<NPL, SYN> &sc, const Wo
   const int bi = mine ? sc.perm()[r] : 0;
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
-    const unsigned word = __reduce_or_sync(FULL, (mine && (bi >> 5) == k) ? 1u << (bi & 31) : 0u) ^ h.yb[k];
+    const unsigned word = __reduce_or_sync(FULL, (mine && (bi >> 5) == k) ? 1u << (bi & 31) : 0u) ^ sc.head_at(k);
     if (lane == 0) reinterpret_cast<unsigned *>(sc.cw() + slot * NM)[k] = word;
   }
   if (lane == 0) {
@@ -1097,6 +1101,12 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   const DevOrder &O = code.ord;
   const int cls = code.even ? h.par : -1;
   const int ti = h.c * O.ncls + (code.even ? h.par : 0);
+  if (lane == 0) {
+#pragma unroll
+    for (int k = 0; k < NPL; k++) sc.headv()[k] = h.yb[k];
+    sc.headv()[NPL] = (unsigned)h.c;
+  }
+  __syncwarp();
   const int tb = __ldg(O.base + ti), tc = __ldg(O.count + ti);
   const int qlim = min(P.cap, tc);
   int q = 0, nhit = 0;
@@ -1132,7 +1142,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
         DF part = tmass;
         if (lane <= hl) df_acc(part, mass);
         const DF tq = df_warp_sum(part);
-        const float r2 = remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q + hl, n, h.c, cls, lane, tq, flags);
+        const float r2 = remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q + hl, n, (int)sc.head_at(NPL), cls, lane, tq, flags);
         if (thr_reached(sc, nhit, r2 * LN2_F + code.log_phi, P.thr)) {
           stop_lane = hl;
           lr2 = r2;
@@ -1163,7 +1173,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   // soft output (Corollary + eq. LLRi)
   if (!have_lr2)
     lr2 = (exhausted || P.forney) ? -CUDART_INF_F
-                    : remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q - 1, n, h.c, cls, lane, df_warp_sum(tmass),
+                    : remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q - 1, n, (int)sc.head_at(NPL), cls, lane, df_warp_sum(tmass),
                                                flags);
 #ifdef SG_PHASE_PROFILE
   const long long t3 = clock64();
