@@ -1044,28 +1044,31 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   std::unique_ptr<sg::MixArgs> mp(new (std::nothrow) sg::MixArgs());
   if (!mp) return SOGRAND_ENOMEM;
   sg::MixArgs &m = *mp;
-  int ncls = 0, wstride = 0, dpbytes = 0, all8 = 1;
+  int wstride = 0, dpbytes = 0, all8 = 1;
   double work[sg::MIX_MAX_CLASSES] = {0, 0, 0};
   size_t o_queue[sg::MIX_MAX_CLASSES] = {0, 0, 0}, o_ctrl[sg::MIX_MAX_CLASSES] = {0, 0, 0};
+  // class slot s holds the groups of lane layout 1 << s (groups are in slot order)
+  auto slot_of = [](int npl) { return npl == 1 ? 0 : (npl == 2 ? 1 : 2); };
   for (int x = 0; x < ng; x++) {
     const sogrand_frame_group &G = groups[order[x]];
-    const int npl = npl_of(G.code->n);
-    if (x == 0 || npl != m.cls[ncls - 1].npl) {
-      sg::MixClass &C = m.cls[ncls++];
+    const int npl = npl_of(G.code->n), sl = slot_of(npl);
+    sg::MixClass &C = m.cls[sl];
+    if (!(m.present & (1 << sl))) {
       C = sg::MixClass{};
       C.npl = npl;
       C.g0 = C.g1 = x;
+      m.present |= 1 << sl;
     }
-    sg::MixClass &C = m.cls[ncls - 1];
     m.groups[x].first = C.total;
     C.total += G.n_frames;
     C.g1 = x + 1;
     C.slot_n = std::max(C.slot_n, G.code->n);
     // estimated work of the class: coded bits times word length (sets the home classes only)
-    work[ncls - 1] += (double)G.n_frames * G.code->n * G.code->n * G.code->n;
+    work[sl] += (double)G.n_frames * G.code->n * G.code->n * G.code->n;
     all8 = all8 && G.code->minb == 8;
   }
-  for (int c = 0; c < ncls; c++) {
+  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
+    if (!(m.present & (1 << c))) continue;
     o_queue[c] = bytes;
     bytes += al256((size_t)m.cls[c].total * max_half * sizeof(int32_t));
     o_ctrl[c] = bytes;
@@ -1084,7 +1087,8 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   bytes += al256((size_t)dp_blocks * slice);
   char *mem = nullptr;
   if (scratch_alloc(&mem, bytes, s) != cudaSuccess) return SOGRAND_ENOMEM;
-  for (int c = 0; c < ncls; c++) {
+  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
+    if (!(m.present & (1 << c))) continue;
     m.cls[c].queue = (int32_t *)(mem + o_queue[c]);
     m.cls[c].ctrl = (int32_t *)(mem + o_ctrl[c]);
   }
@@ -1136,7 +1140,11 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
     M.fresh = 1;
   }
   m.ngroups = ng;
-  m.ncls = ncls;
+  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
+    sg::MixClass &C = m.cls[c];
+    C.single = (m.present & (1 << c)) && C.g1 - C.g0 == 1;
+    if (C.single) m.one[c] = m.groups[C.g0];
+  }
   m.max_half = max_half;
   m.wstride = wstride;
   m.dpbytes = dpbytes;
@@ -1151,12 +1159,16 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   // estimated work (a golden-ratio sequence, so that any subset of ids is
   // split in about the same proportion)
   double wsum = 0;
-  for (int c = 0; c < ncls; c++) wsum += work[c];
+  int last = 0;
+  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
+    wsum += work[c];
+    if (work[c] > 0) last = c;
+  }
   for (int t = 0; t < sg::MIX_SM_TABLE; t++) {
     const double u = std::fmod(0.6180339887498949 * (t + 1), 1.0) * wsum;
     double acc = 0;
     int c = 0;
-    while (c + 1 < ncls && u >= acc + work[c]) acc += work[c++];
+    while (c < last && (work[c] == 0 || u >= acc + work[c])) acc += work[c++];
     m.home[t] = (uint8_t)c;
   }
   const bool timed = stats && stats->timing_ms;

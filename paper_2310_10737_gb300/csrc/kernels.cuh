@@ -625,11 +625,13 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
 // __grid_constant__).  List entry e of a class is frame e - G.first of the
 // group G whose range holds it.
 
-// Decode words of class c until its list is done (returns 1) or the launch
-// stops on an error (returns 0).
-template <class SYN, int NPL>
-__device__ __noinline__ int mixed_class(const MixArgs &m, int c, unsigned char *smem, unsigned char *dpb,
-                                        unsigned char *tl, int warp, int lane) {
+// Decode words of class slot c until its list is done (returns 1) or the
+// launch stops on an error (returns 0).  ONE: the class has a single group,
+// read from m.one[c] (c is then a compile-time constant of the caller);
+// otherwise the group of each list entry is looked up in m.groups.
+template <class SYN, int NPL, bool ONE>
+__device__ __forceinline__ int mixed_class(const MixArgs &m, int c, unsigned char *smem, unsigned char *dpb,
+                                           unsigned char *tl, int warp, int lane) {
   const MixClass &C = m.cls[c];
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, m.wstride, dpb, tl);
@@ -643,10 +645,12 @@ __device__ __noinline__ int mixed_class(const MixArgs &m, int c, unsigned char *
     }
     const int64_t e = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // class list entry
     int g = C.g0;
-    if (lane == 0)
-      while (g + 1 < C.g1 && m.groups[g + 1].first <= e) g++;
-    g = __shfl_sync(FULL, g, 0);
-    const MixGroup &G = m.groups[g];
+    if (!ONE) {
+      if (lane == 0)
+        while (g + 1 < C.g1 && m.groups[g + 1].first <= e) g++;
+      g = __shfl_sync(FULL, g, 0);
+    }
+    const MixGroup &G = ONE ? m.one[c] : m.groups[g];
     if (w >= G.code.n) continue;  // a ticket past this code's words
     const int64_t li = e - G.first;
     int64_t f = G.frames ? (int64_t)G.frames[li] : li;
@@ -665,9 +669,9 @@ __device__ __noinline__ int mixed_class(const MixArgs &m, int c, unsigned char *
       f = vc->f;
       e2 = vc->li;
       half = vc->half;
-      g = vc->grp;
+      if (!ONE) g = vc->grp;
     }
-    const MixGroup &G2 = m.groups[g];
+    const MixGroup &G2 = ONE ? m.one[c] : m.groups[g];
     if (lane == 0 && q < 0) atomicExch(G2.a.bad + f, 1);
     __threadfence();  // release this word's L_E and hard decision
     __syncwarp();
@@ -677,6 +681,16 @@ __device__ __noinline__ int mixed_class(const MixArgs &m, int c, unsigned char *
     if (done != G2.code.n - 1) continue;
     frame_after_half<NPL, false>(G2.code, G2.code, G2.a, C.ctrl, C.queue, f, e2, half, sc.W(), lane);
   }
+}
+
+// Class slot S (lane layout 1 << S): the single-group path with compile-time
+// parameter offsets, or the indexed path.
+template <class SYN, int S>
+__device__ __forceinline__ int mixed_slot(const MixArgs &m, unsigned char *smem, unsigned char *dpb, unsigned char *tl,
+                                          int warp, int lane) {
+  constexpr int NPL = 1 << S;
+  if (m.cls[S].single) return mixed_class<SYN, NPL, true>(m, S, smem, dpb, tl, warp, lane);
+  return mixed_class<SYN, NPL, false>(m, S, smem, dpb, tl, warp, lane);
 }
 
 template <class SYN, int MINB>
@@ -691,19 +705,17 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_consta
   unsigned smid;
   asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
   int c = m.home[smid % MIX_SM_TABLE];
-  unsigned done = 0;
-  const unsigned all = (1u << m.ncls) - 1u;
-  while (done != all) {
-    if ((done >> c) & 1u) {
-      c = c + 1 == m.ncls ? 0 : c + 1;
+  unsigned left = (unsigned)m.present;
+  while (left) {
+    if (!((left >> c) & 1u)) {
+      c = c + 1 == MIX_MAX_CLASSES ? 0 : c + 1;
       continue;
     }
-    const int npl = m.cls[c].npl;
-    const int ok = npl == 1 ? mixed_class<SYN, 1>(m, c, smem, dpb, tl, warp, lane)
-                            : (npl == 2 ? mixed_class<SYN, 2>(m, c, smem, dpb, tl, warp, lane)
-                                        : mixed_class<SYN, 4>(m, c, smem, dpb, tl, warp, lane));
+    const int ok = c == 0 ? mixed_slot<SYN, 0>(m, smem, dpb, tl, warp, lane)
+                          : (c == 1 ? mixed_slot<SYN, 1>(m, smem, dpb, tl, warp, lane)
+                                    : mixed_slot<SYN, 2>(m, smem, dpb, tl, warp, lane));
     if (!ok) break;
-    done |= 1u << c;
+    left &= ~(1u << c);
   }
   tally_flush(tslot, m.wsum, m.xf_count, lane);
 }
@@ -714,8 +726,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_consta
 // With per-frame half_stop arrays, a frame parks after `epoch_halves` halves
 // of this launch.
 static __global__ void k_mixed_init(const __grid_constant__ MixArgs m, int epoch_halves) {
-  for (int c = 0; c < m.ncls; c++) {
+  for (int c = 0; c < MIX_MAX_CLASSES; c++) {
     const MixClass &C = m.cls[c];
+    if (C.total <= 0) continue;
     const int64_t slots = C.total * (int64_t)m.max_half;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
       if (i >= C.total) {
@@ -908,7 +921,7 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
 template <class SYN, int MINB>
 cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_t s) {
   int64_t slots = 0, words = 0;
-  for (int c = 0; c < m.ncls; c++) slots = std::max<int64_t>(slots, m.cls[c].total * m.max_half);
+  for (int c = 0; c < MIX_MAX_CLASSES; c++) slots = std::max<int64_t>(slots, m.cls[c].total * m.max_half);
   for (int g = 0; g < m.ngroups; g++) words += m.groups[g].count * m.groups[g].code.n;
   if (words <= 0) return cudaSuccess;
   k_mixed_init<<<(int)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, s>>>(

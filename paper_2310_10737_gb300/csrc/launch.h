@@ -87,24 +87,29 @@ struct MixGroup {
 };
 
 constexpr int MIX_MAX_GROUPS = 16;
-constexpr int MIX_MAX_CLASSES = 3;
-constexpr int MIX_SM_TABLE = 256;  // home classes by %smid (modulo this size)
+constexpr int MIX_MAX_CLASSES = 3;  // class slot s holds the codes of NPL = 1 << s
+constexpr int MIX_SM_TABLE = 256;   // home classes by %smid (modulo this size)
 
 struct MixClass {
   int32_t *queue;   // [total * max_half] the class's frame-half list: +-(list entry + 1) once filled
   int32_t *ctrl;    // [4] slots reserved, word tickets, frames finished (or parked); [3] unused
-  int64_t total;    // frames of the class
+  int64_t total;    // frames of the class (0: no such class in the launch)
   int32_t slot_n;   // word tickets per list slot: the largest n of the class's codes
   int32_t npl;      // lane layout of the class
   int32_t g0, g1;   // its groups: groups[g0 .. g1), ordered by `first`
+  int32_t single;   // 1: one group, whose parameters are also in MixArgs::one[slot]
 };
 
-// Passed by value as a __grid_constant__ kernel parameter: the kernels index
-// the group table in parameter space (no copy to shared or local memory).
+// Passed by value as a __grid_constant__ kernel parameter.  A class with a
+// single group reads that group's parameters from one[slot], at offsets known
+// when the kernel is compiled (like any kernel parameter); a class of several
+// codes indexes groups[] at run time.
 struct MixArgs {
+  MixGroup one[MIX_MAX_CLASSES];
   MixGroup groups[MIX_MAX_GROUPS];
-  MixClass cls[MIX_MAX_CLASSES];
-  int32_t ngroups, ncls;
+  MixClass cls[MIX_MAX_CLASSES];  // by slot
+  int32_t ngroups;
+  int32_t present;                // bit s: class slot s has frames
   int32_t max_half;        // the largest 2 * max iterations
   int32_t wstride;         // shared bytes per warp: the largest per-warp layout of the classes
   int32_t dpbytes;         // the block's remaining-mass area: the largest of the groups
