@@ -1143,7 +1143,6 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
   for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
     sg::MixClass &C = m.cls[c];
     C.single = (m.present & (1 << c)) && C.g1 - C.g0 == 1;
-    if (C.single) m.one[c] = m.groups[C.g0];
   }
   m.max_half = max_half;
   m.wstride = wstride;

@@ -627,11 +627,11 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
 
 // Decode words of class slot c until its list is done (returns 1) or the
 // launch stops on an error (returns 0).  ONE: the class has a single group,
-// read from m.one[c] (c is then a compile-time constant of the caller);
-// otherwise the group of each list entry is looked up in m.groups.
+// `one` (a by-value kernel parameter of the slot); otherwise the group of each
+// list entry is looked up in m.groups.
 template <class SYN, int NPL, bool ONE>
-__device__ __forceinline__ int mixed_class(const MixArgs &m, int c, unsigned char *smem, unsigned char *dpb,
-                                           unsigned char *tl, int warp, int lane) {
+__device__ __forceinline__ int mixed_class(const MixArgs &m, const MixGroup &one, int c, unsigned char *smem,
+                                           unsigned char *dpb, unsigned char *tl, int warp, int lane) {
   const MixClass &C = m.cls[c];
   Scratch<NPL, SYN> sc;
   bind_scratch(sc, smem, warp, m.wstride, dpb, tl);
@@ -650,7 +650,7 @@ __device__ __forceinline__ int mixed_class(const MixArgs &m, int c, unsigned cha
         while (g + 1 < C.g1 && m.groups[g + 1].first <= e) g++;
       g = __shfl_sync(FULL, g, 0);
     }
-    const MixGroup &G = ONE ? m.one[c] : m.groups[g];
+    const MixGroup &G = ONE ? one : m.groups[g];
     if (w >= G.code.n) continue;  // a ticket past this code's words
     const int64_t li = e - G.first;
     int64_t f = G.frames ? (int64_t)G.frames[li] : li;
@@ -671,7 +671,7 @@ __device__ __forceinline__ int mixed_class(const MixArgs &m, int c, unsigned cha
       half = vc->half;
       if (!ONE) g = vc->grp;
     }
-    const MixGroup &G2 = ONE ? m.one[c] : m.groups[g];
+    const MixGroup &G2 = ONE ? one : m.groups[g];
     if (lane == 0 && q < 0) atomicExch(G2.a.bad + f, 1);
     __threadfence();  // release this word's L_E and hard decision
     __syncwarp();
@@ -686,15 +686,18 @@ __device__ __forceinline__ int mixed_class(const MixArgs &m, int c, unsigned cha
 // Class slot S (lane layout 1 << S): the single-group path with compile-time
 // parameter offsets, or the indexed path.
 template <class SYN, int S>
-__device__ __forceinline__ int mixed_slot(const MixArgs &m, unsigned char *smem, unsigned char *dpb, unsigned char *tl,
-                                          int warp, int lane) {
+__device__ __forceinline__ int mixed_slot(const MixArgs &m, const MixGroup &one, unsigned char *smem, unsigned char *dpb,
+                                          unsigned char *tl, int warp, int lane) {
   constexpr int NPL = 1 << S;
-  if (m.cls[S].single) return mixed_class<SYN, NPL, true>(m, S, smem, dpb, tl, warp, lane);
-  return mixed_class<SYN, NPL, false>(m, S, smem, dpb, tl, warp, lane);
+  if (m.cls[S].single) return mixed_class<SYN, NPL, true>(m, one, S, smem, dpb, tl, warp, lane);
+  return mixed_class<SYN, NPL, false>(m, one, S, smem, dpb, tl, warp, lane);
 }
 
+// one0 .. one2: the group of class slot 0 .. 2 when that class has one group
+// (unused otherwise)
 template <class SYN, int MINB>
-__global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_constant__ MixArgs m) {
+__global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_constant__ MixArgs m, const MixGroup one0,
+                                                          const MixGroup one1, const MixGroup one2) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   unsigned char *tl = block_tail(smem, m.wstride);
@@ -711,9 +714,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_consta
       c = c + 1 == MIX_MAX_CLASSES ? 0 : c + 1;
       continue;
     }
-    const int ok = c == 0 ? mixed_slot<SYN, 0>(m, smem, dpb, tl, warp, lane)
-                          : (c == 1 ? mixed_slot<SYN, 1>(m, smem, dpb, tl, warp, lane)
-                                    : mixed_slot<SYN, 2>(m, smem, dpb, tl, warp, lane));
+    const int ok = c == 0 ? mixed_slot<SYN, 0>(m, one0, smem, dpb, tl, warp, lane)
+                          : (c == 1 ? mixed_slot<SYN, 1>(m, one1, smem, dpb, tl, warp, lane)
+                                    : mixed_slot<SYN, 2>(m, one2, smem, dpb, tl, warp, lane));
     if (!ok) break;
     left &= ~(1u << c);
   }
@@ -939,7 +942,10 @@ cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_
   int64_t cap = (int64_t)sm_count() * occ;
   if (m.dp_area && m.dp_blocks < cap) cap = m.dp_blocks;
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
-  kern<<<grid, TPB, smem, s>>>(m);
+  MixGroup one[MIX_MAX_CLASSES] = {};
+  for (int c = 0; c < MIX_MAX_CLASSES; c++)
+    if (m.cls[c].single) one[c] = m.groups[m.cls[c].g0];
+  kern<<<grid, TPB, smem, s>>>(m, one[0], one[1], one[2]);
   return cudaGetLastError();
 }
 

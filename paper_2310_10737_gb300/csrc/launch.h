@@ -97,15 +97,14 @@ struct MixClass {
   int32_t slot_n;   // word tickets per list slot: the largest n of the class's codes
   int32_t npl;      // lane layout of the class
   int32_t g0, g1;   // its groups: groups[g0 .. g1), ordered by `first`
-  int32_t single;   // 1: one group, whose parameters are also in MixArgs::one[slot]
+  int32_t single;   // 1: one group, whose parameters are also passed as the kernel's own parameter
 };
 
 // Passed by value as a __grid_constant__ kernel parameter.  A class with a
-// single group reads that group's parameters from one[slot], at offsets known
-// when the kernel is compiled (like any kernel parameter); a class of several
+// single group reads that group's parameters from a separate by-value kernel
+// parameter of its slot (read like any kernel parameter); a class of several
 // codes indexes groups[] at run time.
 struct MixArgs {
-  MixGroup one[MIX_MAX_CLASSES];
   MixGroup groups[MIX_MAX_GROUPS];
   MixClass cls[MIX_MAX_CLASSES];  // by slot
   int32_t ngroups;
