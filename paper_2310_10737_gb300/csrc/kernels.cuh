@@ -685,17 +685,20 @@ __device__ __forceinline__ int mixed_class(const MixArgs &m, const MixGroup &one
 
 // Class slot S (lane layout 1 << S): the single-group path with compile-time
 // parameter offsets, or the indexed path.
-template <class SYN, int S>
+// ALL_ONE: every class of the launch has one group (the kernel then carries
+// no indexed path: half the code, and registers allocated for the three
+// single-group paths alone).
+template <class SYN, int S, bool ALL_ONE>
 __device__ __forceinline__ int mixed_slot(const MixArgs &m, const MixGroup &one, unsigned char *smem, unsigned char *dpb,
                                           unsigned char *tl, int warp, int lane) {
   constexpr int NPL = 1 << S;
-  if (m.cls[S].single) return mixed_class<SYN, NPL, true>(m, one, S, smem, dpb, tl, warp, lane);
+  if (ALL_ONE || m.cls[S].single) return mixed_class<SYN, NPL, true>(m, one, S, smem, dpb, tl, warp, lane);
   return mixed_class<SYN, NPL, false>(m, one, S, smem, dpb, tl, warp, lane);
 }
 
 // one0 .. one2: the group of class slot 0 .. 2 when that class has one group
 // (unused otherwise)
-template <class SYN, int MINB>
+template <class SYN, int MINB, bool ALL_ONE>
 __global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_constant__ MixArgs m, const MixGroup one0,
                                                           const MixGroup one1, const MixGroup one2) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -714,9 +717,9 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_consta
       c = c + 1 == MIX_MAX_CLASSES ? 0 : c + 1;
       continue;
     }
-    const int ok = c == 0 ? mixed_slot<SYN, 0>(m, one0, smem, dpb, tl, warp, lane)
-                          : (c == 1 ? mixed_slot<SYN, 1>(m, one1, smem, dpb, tl, warp, lane)
-                                    : mixed_slot<SYN, 2>(m, one2, smem, dpb, tl, warp, lane));
+    const int ok = c == 0 ? mixed_slot<SYN, 0, ALL_ONE>(m, one0, smem, dpb, tl, warp, lane)
+                          : (c == 1 ? mixed_slot<SYN, 1, ALL_ONE>(m, one1, smem, dpb, tl, warp, lane)
+                                    : mixed_slot<SYN, 2, ALL_ONE>(m, one2, smem, dpb, tl, warp, lane));
     if (!ok) break;
     left &= ~(1u << c);
   }
@@ -923,6 +926,8 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
 // Mixed form.  epoch_halves <= 0: no parking.
 template <class SYN, int MINB>
 cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_t s) {
+  bool all_one = true;
+  for (int c = 0; c < MIX_MAX_CLASSES; c++) all_one = all_one && (m.cls[c].total <= 0 || m.cls[c].single);
   int64_t slots = 0, words = 0;
   for (int c = 0; c < MIX_MAX_CLASSES; c++) slots = std::max<int64_t>(slots, m.cls[c].total * m.max_half);
   for (int g = 0; g < m.ngroups; g++) words += m.groups[g].count * m.groups[g].code.n;
@@ -932,7 +937,7 @@ cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int smem = WARPS_PER_BLOCK * m.wstride + TAIL_BYTES + (m.dp_area ? 0 : m.dpbytes);
-  auto kern = k_product_mixed<SYN, MINB>;
+  auto kern = all_one ? k_product_mixed<SYN, MINB, true> : k_product_mixed<SYN, MINB, false>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;
