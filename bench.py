@@ -185,7 +185,7 @@ def job_rate(world, frames, info_bits_per_frame, steps, ms):
 SERVE_CODES = ["ebch_32_26", "ebch_64_57", "ebch_64_51", "ebch_128_120"]
 
 
-def serving_bench(sg, torch, n_req, loads, seed, epoch_halves=2):
+def serving_bench(sg, torch, n_req, loads, seed, epoch_halves=16):
     """Poisson arrivals of decode requests (code uniform over four eBCH product
     codes, 1..64 frames, Eb/N0 uniform in 2.5..4 dB per request) into the
     continuous-batching server, at several offered loads; and the same arrivals
@@ -227,7 +227,7 @@ def serving_bench(sg, torch, n_req, loads, seed, epoch_halves=2):
                        "alpha 0.5, max 20 iterations",
            "requests": n_req, "info_bits": bits, "epoch_halves": epoch_halves,
            "slots": dict(zip(SERVE_CODES, slots)), "latency": "submission to outputs in host memory",
-           "server": [], "per_request_plain": []}
+           "server": [], "per_request_plain": [], "per_request_batched": []}
 
     def pct(v, q):
         return float(np.percentile(np.array(v), q)) if v else None
@@ -259,23 +259,25 @@ def serving_bench(sg, torch, n_req, loads, seed, epoch_halves=2):
                               "p99_ms": pct(lat, 99), "bits_per_s": bits / span, "launches": st["launches"]})
         log(f"serving: server at {lam:g} req/s: p50 {pct(lat, 50):.2f} ms p99 {pct(lat, 99):.2f} ms, "
             f"{bits / span:.3e} bits/s, {st['launches']} launches")
-        # the same arrivals served one request at a time, plain form (one launch per half)
-        lat = []
-        start = time.perf_counter()
-        for i, (ci, llr, _, _) in enumerate(reqs):
-            a = start + arrive[i]
-            d = a - time.perf_counter()
-            if d > 0:
-                time.sleep(d)
-            o = sg.product_decode(codes[ci], llr.cuda(non_blocking=True), L=L_LIST, query_cap=CAP, alpha=ALPHA,
-                                  max_iter=MAX_ITER, persistent=False, stats=False)
-            o["bits"].cpu()
-            lat.append(1000 * (time.perf_counter() - a))
-        span = time.perf_counter() - start
-        res["per_request_plain"].append({"offered_rps": lam, "achieved_rps": n_req / span, "p50_ms": pct(lat, 50),
-                                         "p99_ms": pct(lat, 99), "bits_per_s": bits / span})
-        log(f"serving: per-request plain at {lam:g} req/s: p50 {pct(lat, 50):.2f} ms p99 {pct(lat, 99):.2f} ms, "
-            f"{bits / span:.3e} bits/s")
+        # the same arrivals served one request at a time: the plain form (one
+        # launch per half) and the batched form (one persistent launch per request)
+        for form, pers in (("per_request_plain", False), ("per_request_batched", True)):
+            lat = []
+            start = time.perf_counter()
+            for i, (ci, llr, _, _) in enumerate(reqs):
+                a = start + arrive[i]
+                d = a - time.perf_counter()
+                if d > 0:
+                    time.sleep(d)
+                o = sg.product_decode(codes[ci], llr.cuda(non_blocking=True), L=L_LIST, query_cap=CAP, alpha=ALPHA,
+                                      max_iter=MAX_ITER, persistent=pers, stats=False)
+                o["bits"].cpu()
+                lat.append(1000 * (time.perf_counter() - a))
+            span = time.perf_counter() - start
+            res[form].append({"offered_rps": lam, "achieved_rps": n_req / span, "p50_ms": pct(lat, 50),
+                              "p99_ms": pct(lat, 99), "bits_per_s": bits / span})
+            log(f"serving: {form.replace('_', ' ')} at {lam:g} req/s: p50 {pct(lat, 50):.2f} ms "
+                f"p99 {pct(lat, 99):.2f} ms, {bits / span:.3e} bits/s")
     for c in codes:
         c.close()
     return res

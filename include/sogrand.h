@@ -304,19 +304,21 @@ typedef struct {
 /*
  * Mixed form of product decoding (Sec. VI turbo decoding of each frame, as
  * product_decode_persistent): frames of up to SOGRAND_MIX_MAX_GROUPS codes of
- * different lengths decoded by ONE persistent launch that shares one
- * frame-half list, so the SMs stay busy across codes (the paper decodes one
- * code at a time; this is a batching form of the same computation).  Every
- * frame's results equal those of product_decode_persistent on that frame
- * alone.  L, query_cap, thr, alpha and max_iter apply to every group.
+ * different lengths decoded by ONE launch of a CUDA graph that holds, on
+ * parallel branches, the batched (persistent) decoder of every group, each
+ * with its own frame-half list.  Each kernel has a full grid; as a kernel's
+ * work runs out its surplus warps leave, and blocks of the other kernels take
+ * the SMs, so one code's tail overlaps the next code's decoding (the paper
+ * decodes one code at a time; this is a batching form of the same
+ * computation).  Every frame's results equal those of
+ * product_decode_persistent on that frame alone.  L, query_cap, thr, alpha
+ * and max_iter apply to every group.
  *   groups   HOST [n_groups] (read during the call)
- *   stats    optional: weight_sum, xf_words, timing_ms[0] (the launch),
- *            launches (par_queries is ignored)
- * Synchronous on `stream` (reads the kernel's status).  Errors: EINVAL (as
+ *   stats    optional: weight_sum, xf_words, timing_ms[0] (the graph
+ *            launch), launches (1: the graph launch; par_queries is ignored)
+ * Synchronous on `stream` (reads the kernels' status).  Errors: EINVAL (as
  * product_decode_persistent for any group, n_groups outside
- * 1..SOGRAND_MIX_MAX_GROUPS, total frames x 2 max_iter x 128 >= 2^31),
- * EUNSUPPORTED (groups whose codes need different syndrome widths: n - k <= 32
- * and n - k > 32 in one call), ENOMEM, ECUDA, ETIMEOUT.
+ * 1..SOGRAND_MIX_MAX_GROUPS), ENOMEM, ECUDA, ETIMEOUT.
  */
 int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L, int64_t query_cap, float thr,
                          float alpha, int max_iter, product_decode_stats *stats, void *stream);

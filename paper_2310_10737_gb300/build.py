@@ -21,7 +21,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT, "libsogrand.so")
 SOURCES = ["abi.cu", "inst_npl1.cu", "inst_npl2.cu", "inst_npl4.cu", "inst_npl1_gen.cu", "inst_npl2_gen.cu",
-           "inst_npl4_gen.cu", "inst_mixed.cu", "inst_mixed8.cu", "peak.cu", "server.cu"]
+           "inst_npl4_gen.cu", "peak.cu", "server.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -414,11 +414,6 @@ int sm_count_of_device() {
 }  // namespace sgi
 
 namespace sg {
-int warp_area_bytes(int npl, int syn_bytes) {
-  if (npl == 1) return syn_bytes == 4 ? Layout<1, uint32_t>::warp_bytes : Layout<1, uint64_t>::warp_bytes;
-  if (npl == 2) return syn_bytes == 4 ? Layout<2, uint32_t>::warp_bytes : Layout<2, uint64_t>::warp_bytes;
-  return syn_bytes == 4 ? Layout<4, uint32_t>::warp_bytes : Layout<4, uint64_t>::warp_bytes;
-}
 int dp_area_bytes(int npl, int syn_bytes, int jmax) {
   if (npl == 1) return syn_bytes == 4 ? Layout<1, uint32_t>::dp_bytes(jmax) : Layout<1, uint64_t>::dp_bytes(jmax);
   if (npl == 2) return syn_bytes == 4 ? Layout<2, uint32_t>::dp_bytes(jmax) : Layout<2, uint64_t>::dp_bytes(jmax);
@@ -717,7 +712,7 @@ size_t persistent_scratch_bytes(int64_t F, int nr, int nc, int nm, int max_iter)
   return al256((size_t)F * nr * nc * sizeof(float)) + al256((size_t)F * std::max(nr, nc) * nm * sizeof(uint64_t)) +
          5 * al256(b_i32) +
          al256((size_t)F * 2 * max_iter * sizeof(int32_t)) + 2 * al256(b_i64) + al256((size_t)F) +
-         al256(4 * sizeof(int32_t));
+         al256(8 * sizeof(int32_t));
 }
 
 // The global remaining-mass region of a persistent launch: one slice per
@@ -766,7 +761,7 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   int64_t *q_s = (int64_t *)take(b_i64);
   int64_t *pq_s = (int64_t *)take(b_i64);
   uint8_t *st_s = (uint8_t *)take((size_t)F);
-  a.ctrl = (int32_t *)take(4 * sizeof(int32_t));
+  a.ctrl = (int32_t *)take(8 * sizeof(int32_t));
   a.bits = bits;
   a.half_iters = half_iters ? half_iters : hi_s;
   a.queries = queries ? queries : q_s;
@@ -999,201 +994,122 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   return SOGRAND_OK;
 }
 
+}  // extern "C"
+
+namespace {
+// The mixed form as one CUDA graph: a persistent decoder kernel per group
+// (each the single-code batched kernel of its code, with its own frame-half
+// list) on parallel branches, launched with one cudaGraphLaunch.  Every
+// kernel gets a full grid; the hardware starts blocks of the next kernel as
+// blocks of an earlier one leave, and a kernel's warps leave as soon as its
+// unfinished frames cannot use them, so the tail of one code's decode
+// overlaps the start of the next and no SM idles while any code has work.
+int mixed_graph_decode(int n_groups, const sogrand_frame_group *groups, int L, int64_t cap, float thr, float alpha,
+                       int max_iter, product_decode_stats *stats, cudaStream_t s) {
+  std::vector<int> live;
+  for (int g = 0; g < n_groups; g++)
+    if (groups[g].n_frames > 0) live.push_back(g);
+  const int k = (int)live.size();
+  // scratch of every group's batched decode, with its remaining-mass region
+  std::vector<size_t> off(k + 1, 0);
+  for (int x = 0; x < k; x++) {
+    const sogrand_frame_group &G = groups[live[x]];
+    off[x + 1] = off[x] + al256(persistent_scratch_bytes(G.n_frames, G.code->n, G.code->n, G.code->nm, max_iter)) +
+                 dp_region_bytes(G.code, G.code);
+  }
+  const size_t o_err = off[k];
+  char *mem = nullptr;
+  if (scratch_alloc(&mem, o_err + 256, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  int32_t *d_err = (int32_t *)(mem + o_err);  // one timeout flag per kernel
+  const sg::SisoParams P = siso_params(L, cap, thr);
+  std::vector<cudaStream_t> st(k, nullptr);
+  std::vector<cudaEvent_t> ev;
+  cudaError_t e = cudaSuccess;
+  for (int x = 0; x < k && e == cudaSuccess; x++) e = cudaStreamCreateWithFlags(&st[x], cudaStreamNonBlocking);
+  auto event = [&ev, &e]() {
+    cudaEvent_t x = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
+    if (x) ev.push_back(x);
+    return x;
+  };
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(st[0], cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaEvent_t fork = event();
+    if (e == cudaSuccess) e = cudaEventRecord(fork, st[0]);
+    for (int x = 1; x < k && e == cudaSuccess; x++) e = cudaStreamWaitEvent(st[x], fork, 0);
+    for (int x = 0; x < k && e == cudaSuccess; x++) {
+      const sogrand_frame_group &G = groups[live[x]];
+      int32_t *err_x = nullptr;
+      e = persistent_enqueue(G.code, G.code, G.n_frames, G.llr_ch, P, alpha, max_iter, G.bits, G.half_iters, G.status,
+                             G.queries, nullptr, stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr,
+                             stats ? stats->xf_words : nullptr, mem + off[x], st[x], &err_x);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(d_err + x, err_x, sizeof(int32_t), cudaMemcpyDeviceToDevice, st[x]);
+    }
+    for (int x = 1; x < k && e == cudaSuccess; x++) {
+      cudaEvent_t join = event();
+      if (e == cudaSuccess) e = cudaEventRecord(join, st[x]);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(st[0], join, 0);
+    }
+    const cudaError_t ec = cudaStreamEndCapture(st[0], &graph);
+    if (e == cudaSuccess) e = ec;
+  }
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
+  const bool timed = stats && stats->timing_ms;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;  // timed events (the others have timing disabled)
+  if (e == cudaSuccess && timed) {
+    e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+  }
+  if (t0) ev.push_back(t0);
+  if (t1) ev.push_back(t1);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(t0, s);
+  if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
+  if (e == cudaSuccess && timed) e = cudaEventRecord(t1, s);
+  std::vector<int32_t> err(k, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(err.data(), d_err, k * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess && timed) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, t0, t1);
+    stats->timing_ms[0] = ms;
+  }
+  if (stats && stats->launches) stats->launches[0] = 1;  // one graph launch (an init and a decoder kernel per code)
+  if (exec) cudaGraphExecDestroy(exec);
+  if (graph) cudaGraphDestroy(graph);
+  for (cudaEvent_t x : ev) cudaEventDestroy(x);
+  for (cudaStream_t x : st)
+    if (x) cudaStreamDestroy(x);
+  const cudaError_t e2 = cudaFreeAsync(mem, s);
+  if (e != cudaSuccess || e2 != cudaSuccess) return SOGRAND_ECUDA;
+  for (int32_t x : err)
+    if (x) return SOGRAND_ETIMEOUT;
+  return SOGRAND_OK;
+}
+}  // namespace
+
+extern "C" {
+
 int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L, int64_t cap, float thr, float alpha,
                          int max_iter, product_decode_stats *stats, void *stream) {
   if (stats && stats->timing_ms) stats->timing_ms[0] = stats->timing_ms[1] = 0.f;
   if (stats && stats->launches) stats->launches[0] = 0;
-  static_assert(SOGRAND_MIX_MAX_GROUPS == sg::MIX_MAX_GROUPS, "group table size");
   if (n_groups < 1 || n_groups > SOGRAND_MIX_MAX_GROUPS || !groups) return SOGRAND_EINVAL;
   int64_t total = 0;
-  int syn64 = -1;
   for (int g = 0; g < n_groups; g++) {
     const sogrand_frame_group &G = groups[g];
     int rc = persistent_check(G.code, G.code, G.n_frames, L, cap, thr, alpha, max_iter);
     if (rc != SOGRAND_OK) return rc;
     if (G.n_frames > 0 && (!G.llr_ch || !G.bits)) return SOGRAND_EINVAL;
-    const int s64 = G.code->m > 32 ? 1 : 0;
-    if (syn64 >= 0 && s64 != syn64) return SOGRAND_EUNSUPPORTED;  // one syndrome width per launch
-    syn64 = s64;
     total += G.n_frames;
   }
-  if (total * 2 * (int64_t)max_iter * 128 >= (int64_t(1) << 31) - (int64_t(1) << 22)) return SOGRAND_EINVAL;
   if (total == 0) return SOGRAND_OK;
   for (int g = 0; g < n_groups; g++) {
     int rc = ensure_cap(groups[g].code, cap);
     if (rc != SOGRAND_OK) return rc;
   }
-  cudaStream_t s = (cudaStream_t)stream;
-  const int max_half = 2 * max_iter;
-  auto npl_of = [](int n) { return n <= 32 ? 1 : (n <= 64 ? 2 : 4); };
-  // groups with frames, ordered by class (lane layout), then as given
-  std::vector<int> order;
-  for (int npl : {1, 2, 4})
-    for (int g = 0; g < n_groups; g++)
-      if (groups[g].n_frames > 0 && npl_of(groups[g].code->n) == npl) order.push_back(g);
-  const int ng = (int)order.size();
-  // scratch: per group the persistent-form buffers, then per class its list
-  // and control words, then the launch's error word
-  std::vector<size_t> off(ng);
-  size_t bytes = 0;
-  for (int x = 0; x < ng; x++) {
-    const sogrand_frame_group &G = groups[order[x]];
-    off[x] = bytes;
-    bytes += al256(persistent_scratch_bytes(G.n_frames, G.code->n, G.code->n, G.code->nm, max_iter));
-  }
-  std::unique_ptr<sg::MixArgs> mp(new (std::nothrow) sg::MixArgs());
-  if (!mp) return SOGRAND_ENOMEM;
-  sg::MixArgs &m = *mp;
-  int wstride = 0, dpbytes = 0, all8 = 1;
-  double work[sg::MIX_MAX_CLASSES] = {0, 0, 0};
-  size_t o_queue[sg::MIX_MAX_CLASSES] = {0, 0, 0}, o_ctrl[sg::MIX_MAX_CLASSES] = {0, 0, 0};
-  // class slot s holds the groups of lane layout 1 << s (groups are in slot order)
-  auto slot_of = [](int npl) { return npl == 1 ? 0 : (npl == 2 ? 1 : 2); };
-  for (int x = 0; x < ng; x++) {
-    const sogrand_frame_group &G = groups[order[x]];
-    const int npl = npl_of(G.code->n), sl = slot_of(npl);
-    sg::MixClass &C = m.cls[sl];
-    if (!(m.present & (1 << sl))) {
-      C = sg::MixClass{};
-      C.npl = npl;
-      C.g0 = C.g1 = x;
-      m.present |= 1 << sl;
-    }
-    m.groups[x].first = C.total;
-    C.total += G.n_frames;
-    C.g1 = x + 1;
-    C.slot_n = std::max(C.slot_n, G.code->n);
-    // estimated work of the class: coded bits times word length (sets the home classes only)
-    work[sl] += (double)G.n_frames * G.code->n * G.code->n * G.code->n;
-    all8 = all8 && G.code->minb == 8;
-  }
-  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
-    if (!(m.present & (1 << c))) continue;
-    o_queue[c] = bytes;
-    bytes += al256((size_t)m.cls[c].total * max_half * sizeof(int32_t));
-    o_ctrl[c] = bytes;
-    bytes += 256;
-  }
-  const size_t o_err = bytes;
-  bytes += 256;
-  // the blocks' remaining-mass areas, one slice per resident block
-  int slice = 0;
-  for (int x = 0; x < ng; x++) {
-    const sogrand_code *c = groups[order[x]].code;
-    slice = std::max(slice, sg::dp_slice_bytes(npl_of(c->n), syn64 ? 8 : 4, c->jmax));
-  }
-  const size_t o_dp = bytes;
-  const int dp_blocks = sgi::sm_count_of_device() * MAX_BLOCKS_PER_SM;
-  bytes += al256((size_t)dp_blocks * slice);
-  char *mem = nullptr;
-  if (scratch_alloc(&mem, bytes, s) != cudaSuccess) return SOGRAND_ENOMEM;
-  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
-    if (!(m.present & (1 << c))) continue;
-    m.cls[c].queue = (int32_t *)(mem + o_queue[c]);
-    m.cls[c].ctrl = (int32_t *)(mem + o_ctrl[c]);
-  }
-  int32_t *gctrl = (int32_t *)(mem + o_err);  // [3]: the launch's error word
-  for (int x = 0; x < ng; x++) {
-    const sogrand_frame_group &G = groups[order[x]];
-    sogrand_code *c = G.code;
-    const int npl = npl_of(c->n);
-    wstride = std::max(wstride, sg::warp_area_bytes(npl, syn64 ? 8 : 4));
-    dpbytes = std::max(dpbytes, sg::dp_area_bytes(npl, syn64 ? 8 : 4, c->jmax));
-    char *p = mem + off[x];
-    auto take = [&p](size_t b) {
-      char *r = p;
-      p += al256(b);
-      return r;
-    };
-    const int64_t F = G.n_frames;
-    const size_t b_i32 = (size_t)F * 4, b_i64 = (size_t)F * 8;
-    sg::ProductArgs a{};
-    a.n_frames = F;
-    a.llr_ch = G.llr_ch;
-    a.alpha = alpha;
-    a.max_half = max_half;
-    a.le = (float *)take((size_t)F * c->n * c->n * sizeof(float));
-    a.hb = (uint64_t *)take((size_t)F * c->n * c->nm * sizeof(uint64_t));
-    a.hmax = (int32_t *)take(b_i32);
-    a.half_cur = (int32_t *)take(b_i32);
-    a.done_words = (int32_t *)take(b_i32);
-    a.bad = (int32_t *)take(b_i32);
-    take((size_t)F * 2 * max_iter * sizeof(int32_t));  // (the single-code list, unused here)
-    int32_t *hi_s = (int32_t *)take(b_i32);
-    int64_t *q_s = (int64_t *)take(b_i64);
-    int64_t *pq_s = (int64_t *)take(b_i64);
-    uint8_t *st_s = (uint8_t *)take((size_t)F);
-    a.bits = G.bits;
-    a.half_iters = G.half_iters ? G.half_iters : hi_s;
-    a.queries = G.queries ? G.queries : q_s;
-    a.par_queries = pq_s;
-    a.status = G.status ? G.status : st_s;
-    a.nr = a.nc = a.hbw = c->n;
-    a.ctrl = gctrl;  // a remaining-mass lock timeout in a word sets gctrl[3] and stops the launch
-    sg::MixGroup &M = m.groups[x];
-    M.code = dev_code(c);
-    M.P = siso_params(L, cap, thr);
-    M.a = a;
-    M.frames = nullptr;
-    M.count = F;
-    M.npl = npl;
-    M.fresh = 1;
-  }
-  m.ngroups = ng;
-  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
-    sg::MixClass &C = m.cls[c];
-    C.single = (m.present & (1 << c)) && C.g1 - C.g0 == 1;
-  }
-  m.max_half = max_half;
-  m.wstride = wstride;
-  m.dpbytes = dpbytes;
-  m.max_spin = (int32_t)g_queue_wait_us.load();
-  m.err = gctrl + 3;
-  m.dp_area = (unsigned char *)(mem + o_dp);
-  m.dp_stride = slice;
-  m.dp_blocks = dp_blocks;
-  m.xf_count = stats ? stats->xf_words : nullptr;
-  m.wsum = stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr;
-  // home classes: SM ids spread over the classes in proportion to their
-  // estimated work (a golden-ratio sequence, so that any subset of ids is
-  // split in about the same proportion)
-  double wsum = 0;
-  int last = 0;
-  for (int c = 0; c < sg::MIX_MAX_CLASSES; c++) {
-    wsum += work[c];
-    if (work[c] > 0) last = c;
-  }
-  for (int t = 0; t < sg::MIX_SM_TABLE; t++) {
-    const double u = std::fmod(0.6180339887498949 * (t + 1), 1.0) * wsum;
-    double acc = 0;
-    int c = 0;
-    while (c < last && (work[c] == 0 || u >= acc + work[c])) acc += work[c++];
-    m.home[t] = (uint8_t)c;
-  }
-  const bool timed = stats && stats->timing_ms;
-  cudaEvent_t ev[2] = {nullptr, nullptr};
-  cudaError_t e = cudaSuccess;
-  if (timed)
-    for (int i = 0; i < 2 && e == cudaSuccess; i++) e = cudaEventCreate(&ev[i]);
-  if (e == cudaSuccess && timed) e = cudaEventRecord(ev[0], s);
-  if (e == cudaSuccess)
-    e = syn64 ? sg::launch_product_mixed<uint64_t, 6>(m, 0, s)
-              : (all8 ? sg::launch_product_mixed<uint32_t, 8>(m, 0, s) : sg::launch_product_mixed<uint32_t, 6>(m, 0, s));
-  if (e == cudaSuccess && timed) e = cudaEventRecord(ev[1], s);
-  int32_t err = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&err, m.err, sizeof(int32_t), cudaMemcpyDeviceToHost, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  if (e == cudaSuccess && timed) {
-    float x = 0.f;
-    e = cudaEventElapsedTime(&x, ev[0], ev[1]);
-    stats->timing_ms[0] = x;
-  }
-  for (int i = 0; i < 2; i++)
-    if (ev[i]) cudaEventDestroy(ev[i]);
-  if (stats && stats->launches) stats->launches[0] = 2;
-  cudaError_t e2 = cudaFreeAsync(mem, s);
-  if (e != cudaSuccess || e2 != cudaSuccess) return SOGRAND_ECUDA;
-  return err ? SOGRAND_ETIMEOUT : SOGRAND_OK;
+  return mixed_graph_decode(n_groups, groups, L, cap, thr, alpha, max_iter, stats, (cudaStream_t)stream);
 }
 
 int product_decode(sogrand_code *row_code, const sogrand_code *col_code, int64_t n_frames, const float *llr_ch, int L,

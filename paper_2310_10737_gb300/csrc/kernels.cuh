@@ -181,7 +181,6 @@ __device__ __forceinline__ void tally_flush(const unsigned long long *slot, unsi
 struct WordCtx {
   int64_t f, li;
   int32_t wd, half;
-  int32_t grp;  // mixed form: the word's group
 };
 static_assert(sizeof(WordCtx) <= 32, "the word's lambda follows the context in the frame-check area");
 
@@ -464,7 +463,7 @@ __global__ void __launch_bounds__(TPB) k_product_check(const DevCode rowc, const
 // broadcast, so the whole warp takes the same branch.
 __device__ __forceinline__ int sched_take(int32_t *ctrl_w, int32_t *err_w, const volatile int32_t *queue,
                                           int64_t nslots, int64_t frames, int slot_n, int max_spin, int lane,
-                                          int *slot_out, int *word_out, int *f1_out) {
+                                          int *slot_out, int *word_out, int *f1_out, int *waited) {
   volatile int32_t *ctrl = ctrl_w;  // [0] slots reserved, [1] word tickets, [2] finished frames
   const volatile int32_t *err = err_w;
   int ticket = 0;
@@ -488,6 +487,7 @@ __device__ __forceinline__ int sched_take(int32_t *ctrl_w, int32_t *err_w, const
     }
     st = __shfl_sync(FULL, st, 0);
     if (st != 0) break;
+    *waited = 1;
     if (slept > (long long)max_spin * 1000) {
       if (lane == 0) atomicExch(err_w, 1);
       st = 2;
@@ -578,9 +578,31 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
   const int slot_n = GEN ? max(a.nr, a.nc) : rowc.n;  // tickets per list slot: the most words in a half
   const int64_t nslots = a.n_frames * (int64_t)a.max_half;  // a frame has at most max_half halves
   tally_clear(sc.tally(), lane);
+  if (lane == 0) atomicAdd(a.ctrl + 4, 1);  // one more active warp
+  int waited = 0;
   for (;;) {
+    // Drain: a warp leaves once the unfinished frames cannot use it (each has
+    // at most slot_n words in flight), so the SMs go to other work sharing
+    // the GPU (the parallel kernels of the mixed form); the warps that stay
+    // can always take every word that becomes available.  Decided before a
+    // ticket is drawn (a drawn ticket is always decoded), and only once the
+    // warp has had to wait for work: while the list runs ahead of the
+    // tickets the check is skipped.
+    int leave = 0;
+    if (waited && lane == 0) {
+      const int64_t need = (a.n_frames - (int64_t)__ldcg(a.ctrl + 2)) * slot_n;
+      if ((int64_t)__ldcg(a.ctrl + 4) - 1 >= need) {
+        if ((int64_t)atomicSub(a.ctrl + 4, 1) - 1 >= need)
+          leave = 1;
+        else
+          atomicAdd(a.ctrl + 4, 1);
+      }
+    }
+    if (__shfl_sync(FULL, leave, 0)) break;
     int slot, w, f1;
-    if (!sched_take(a.ctrl, a.ctrl + 3, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1)) break;
+    if (!sched_take(a.ctrl, a.ctrl + 3, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1,
+                    &waited))
+      break;
     const bool rows = f1 > 0;                      // the slot's half is odd: a row half
     int64_t li = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // list index
     const DevCode &code = GEN ? (rows ? rowc : colc) : rowc, &xcode = GEN ? (rows ? colc : rowc) : rowc;
@@ -610,161 +632,6 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
     frame_after_half<NPL, GEN>(code, xcode, a, a.ctrl, a.queue, f, li, half, sc.W(), lane);
   }
   tally_flush(sc.tally(), a.wsum, a.xf_count, lane);
-}
-
-// ---- mixed form: frames of several codes (uneven n) in one launch ----
-// The groups (one code each) are split into classes by lane layout; every
-// class has its own frame-half list and ticket counter, exactly as a
-// persistent launch of its own, and runs the instantiation of its NPL.  Every
-// SM has a home class (by %smid): its warps take tickets of that class while
-// the class has work, so an SM runs one code path and the instruction caches
-// hold one path (warps of different classes on one SM stalled on instruction
-// fetch); a warp whose class has finished moves on to the next class that has
-// not, so no SM idles while any class has work.  Group parameters are read
-// from the kernel's parameter space by group index (the MixArgs parameter is
-// __grid_constant__).  List entry e of a class is frame e - G.first of the
-// group G whose range holds it.
-
-// Decode words of class slot c until its list is done (returns 1) or the
-// launch stops on an error (returns 0).  ONE: the class has a single group,
-// `one` (a by-value kernel parameter of the slot); otherwise the group of each
-// list entry is looked up in m.groups.
-template <class SYN, int NPL, bool ONE>
-__device__ __forceinline__ int mixed_class(const MixArgs &m, const MixGroup &one, int c, unsigned char *smem,
-                                           unsigned char *dpb, unsigned char *tl, int warp, int lane) {
-  const MixClass &C = m.cls[c];
-  Scratch<NPL, SYN> sc;
-  bind_scratch(sc, smem, warp, m.wstride, dpb, tl);
-  const int64_t nslots = C.total * (int64_t)m.max_half;
-  for (;;) {
-    int slot, w, f1;
-    if (!sched_take(C.ctrl, m.err, C.queue, nslots, C.total, C.slot_n, m.max_spin, lane, &slot, &w, &f1)) {
-      int bad = 0;
-      if (lane == 0) bad = *reinterpret_cast<volatile int32_t *>(m.err);
-      return __shfl_sync(FULL, bad, 0) == 0;
-    }
-    const int64_t e = (int64_t)(f1 > 0 ? f1 : -f1) - 1;  // class list entry
-    int g = C.g0;
-    if (!ONE) {
-      if (lane == 0)
-        while (g + 1 < C.g1 && m.groups[g + 1].first <= e) g++;
-      g = __shfl_sync(FULL, g, 0);
-    }
-    const MixGroup &G = ONE ? one : m.groups[g];
-    if (w >= G.code.n) continue;  // a ticket past this code's words
-    const int64_t li = e - G.first;
-    int64_t f = G.frames ? (int64_t)G.frames[li] : li;
-    int half = 0;
-    if (lane == 0) {
-      half = __ldcg(G.a.half_cur + f);
-      WordCtx *ctx = reinterpret_cast<WordCtx *>(sc.W());
-      ctx->li = e;
-      ctx->grp = g;
-    }
-    half = __shfl_sync(FULL, half, 0);
-    const int q = product_word<NPL, SYN, true, false, false>(G.code, G.P, G.a, sc, f, w, half, lane);
-    int64_t e2;
-    {
-      const volatile WordCtx *vc = reinterpret_cast<const volatile WordCtx *>(sc.W());
-      f = vc->f;
-      e2 = vc->li;
-      half = vc->half;
-      if (!ONE) g = vc->grp;
-    }
-    const MixGroup &G2 = ONE ? one : m.groups[g];
-    if (lane == 0 && q < 0) atomicExch(G2.a.bad + f, 1);
-    __threadfence();  // release this word's L_E and hard decision
-    __syncwarp();
-    int done = 0;
-    if (lane == 0) done = atomicAdd(G2.a.done_words + f, 1);
-    done = __shfl_sync(FULL, done, 0);
-    if (done != G2.code.n - 1) continue;
-    frame_after_half<NPL, false>(G2.code, G2.code, G2.a, C.ctrl, C.queue, f, e2, half, sc.W(), lane);
-  }
-}
-
-// Class slot S (lane layout 1 << S): the single-group path with compile-time
-// parameter offsets, or the indexed path.
-// ALL_ONE: every class of the launch has one group (the kernel then carries
-// no indexed path: half the code, and registers allocated for the three
-// single-group paths alone).
-template <class SYN, int S, bool ALL_ONE>
-__device__ __forceinline__ int mixed_slot(const MixArgs &m, const MixGroup &one, unsigned char *smem, unsigned char *dpb,
-                                          unsigned char *tl, int warp, int lane) {
-  constexpr int NPL = 1 << S;
-  if (ALL_ONE || m.cls[S].single) return mixed_class<SYN, NPL, true>(m, one, S, smem, dpb, tl, warp, lane);
-  return mixed_class<SYN, NPL, false>(m, one, S, smem, dpb, tl, warp, lane);
-}
-
-// one0 .. one2: the group of class slot 0 .. 2 when that class has one group
-// (unused otherwise)
-template <class SYN, int MINB, bool ALL_ONE>
-__global__ void __launch_bounds__(TPB, MINB) k_product_mixed(const __grid_constant__ MixArgs m, const MixGroup one0,
-                                                          const MixGroup one1, const MixGroup one2) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  unsigned char *tl = block_tail(smem, m.wstride);
-  unsigned char *dpb = block_dp_area(smem, m.wstride, m.dp_area, m.dp_stride);
-  init_block_lock(tl, m.groups[0].P);
-  unsigned long long *tslot = reinterpret_cast<unsigned long long *>(tl + 16) + 2 * warp;
-  tally_clear(tslot, lane);
-  unsigned smid;
-  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
-  int c = m.home[smid % MIX_SM_TABLE];
-  unsigned left = (unsigned)m.present;
-  while (left) {
-    if (!((left >> c) & 1u)) {
-      c = c + 1 == MIX_MAX_CLASSES ? 0 : c + 1;
-      continue;
-    }
-    const int ok = c == 0 ? mixed_slot<SYN, 0, ALL_ONE>(m, one0, smem, dpb, tl, warp, lane)
-                          : (c == 1 ? mixed_slot<SYN, 1, ALL_ONE>(m, one1, smem, dpb, tl, warp, lane)
-                                    : mixed_slot<SYN, 2, ALL_ONE>(m, one2, smem, dpb, tl, warp, lane));
-    if (!ok) break;
-    left &= ~(1u << c);
-  }
-  tally_flush(tslot, m.wsum, m.xf_count, lane);
-}
-
-// Lists and counters of the mixed form: every listed frame queued in its
-// class's list for its current half.  Frames of groups marked `fresh` start
-// at half 1 with cleared counters; others resume where they were parked.
-// With per-frame half_stop arrays, a frame parks after `epoch_halves` halves
-// of this launch.
-static __global__ void k_mixed_init(const __grid_constant__ MixArgs m, int epoch_halves) {
-  for (int c = 0; c < MIX_MAX_CLASSES; c++) {
-    const MixClass &C = m.cls[c];
-    if (C.total <= 0) continue;
-    const int64_t slots = C.total * (int64_t)m.max_half;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < slots; i += (int64_t)gridDim.x * blockDim.x) {
-      if (i >= C.total) {
-        C.queue[i] = 0;
-        continue;
-      }
-      int g = C.g0;
-      while (g + 1 < C.g1 && m.groups[g + 1].first <= i) g++;
-      const MixGroup &G = m.groups[g];
-      const int64_t li = i - G.first;
-      const int64_t f = G.frames ? (int64_t)G.frames[li] : li;
-      if (G.fresh) {
-        G.a.half_cur[f] = 1;
-        G.a.bad[f] = 0;
-        G.a.queries[f] = 0;
-        G.a.par_queries[f] = 0;
-      }
-      G.a.done_words[f] = 0;
-      G.a.hmax[f] = 0;
-      if (G.a.half_stop) G.a.half_stop[f] = G.a.half_cur[f] + epoch_halves - 1;
-      C.queue[i] = (G.a.half_cur[f] & 1) ? (int32_t)(i + 1) : -(int32_t)(i + 1);
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0) {
-      C.ctrl[0] = (int32_t)C.total;  // next slot to reserve
-      C.ctrl[1] = 0;                 // word tickets drawn
-      C.ctrl[2] = 0;                 // frames finished or parked
-      C.ctrl[3] = 0;
-    }
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *m.err = 0;
 }
 
 // list and counters of the persistent form: every frame queued for half 1
@@ -801,6 +668,7 @@ static __global__ void k_persistent_init(const ProductArgs a) {
     a.ctrl[1] = 0;           // word tickets drawn
     a.ctrl[2] = 0;           // frames finished
     a.ctrl[3] = 0;           // error
+    a.ctrl[4] = 0;           // active warps
   }
 }
 
@@ -920,37 +788,6 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   if (a.dp_area && a.dp_blocks < cap) cap = a.dp_blocks;  // one slice of the region per block
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
   kern<<<grid, TPB, smem, s>>>(rowc, colc, P, a);
-  return cudaGetLastError();
-}
-
-// Mixed form.  epoch_halves <= 0: no parking.
-template <class SYN, int MINB>
-cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_t s) {
-  bool all_one = true;
-  for (int c = 0; c < MIX_MAX_CLASSES; c++) all_one = all_one && (m.cls[c].total <= 0 || m.cls[c].single);
-  int64_t slots = 0, words = 0;
-  for (int c = 0; c < MIX_MAX_CLASSES; c++) slots = std::max<int64_t>(slots, m.cls[c].total * m.max_half);
-  for (int g = 0; g < m.ngroups; g++) words += m.groups[g].count * m.groups[g].code.n;
-  if (words <= 0) return cudaSuccess;
-  k_mixed_init<<<(int)std::min<int64_t>((slots + 255) / 256, 4096), 256, 0, s>>>(
-      m, epoch_halves > 0 ? epoch_halves : m.max_half);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  const int smem = WARPS_PER_BLOCK * m.wstride + TAIL_BYTES + (m.dp_area ? 0 : m.dpbytes);
-  auto kern = all_one ? k_product_mixed<SYN, MINB, true> : k_product_mixed<SYN, MINB, false>;
-  e = set_smem(kern, smem);
-  if (e != cudaSuccess) return e;
-  int occ = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, TPB, smem);
-  if (occ < 1) occ = 1;
-  const int64_t want = (words + WARPS_PER_BLOCK - 1) / WARPS_PER_BLOCK;
-  int64_t cap = (int64_t)sm_count() * occ;
-  if (m.dp_area && m.dp_blocks < cap) cap = m.dp_blocks;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
-  MixGroup one[MIX_MAX_CLASSES] = {};
-  for (int c = 0; c < MIX_MAX_CLASSES; c++)
-    if (m.cls[c].single) one[c] = m.groups[m.cls[c].g0];
-  kern<<<grid, TPB, smem, s>>>(m, one[0], one[1], one[2]);
   return cudaGetLastError();
 }
 

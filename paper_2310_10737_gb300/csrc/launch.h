@@ -53,7 +53,7 @@ struct ProductArgs {
   int32_t *half_cur;          // [F] current half iteration of each frame
   int32_t *done_words;        // [F] words of the current half completed
   int32_t *bad;               // [F] a non-finite input was seen
-  int32_t *ctrl;              // [4] slots reserved, word tickets, finished frames, error
+  int32_t *ctrl;              // [8] slots reserved, word tickets, finished frames, error, active warps
   int32_t max_spin;           // microseconds of accumulated back-off without work before giving up
   int32_t *half_stop;         // [F] or null: park the frame after this half (serving epochs)
   // serving: the launch decodes the frames named by a list (buffer indices;
@@ -70,55 +70,6 @@ struct ProductArgs {
   // shared memory
   unsigned char *dp_area;
   int32_t dp_stride, dp_blocks;
-};
-
-// Mixed form: groups of frames, one code per group, in one launch.  The
-// groups are split into classes by lane layout (bits per lane NPL = 1, 2 or
-// 4); each class has its own frame-half list and ticket counter.
-struct MixGroup {
-  DevCode code;
-  SisoParams P;
-  ProductArgs a;           // the group's buffers, indexed by frame (buffer) index; queue/ctrl unused
-  const int32_t *frames;   // [count] buffer index of each listed frame, or null for 0..count-1
-  int64_t first;           // index of the group's first frame in its class's list
-  int64_t count;           // listed frames
-  int32_t npl;             // bits per lane of the code: 1, 2 or 4
-  int32_t fresh;           // 1: the listed frames start at half 1 with cleared counters
-};
-
-constexpr int MIX_MAX_GROUPS = 16;
-constexpr int MIX_MAX_CLASSES = 3;  // class slot s holds the codes of NPL = 1 << s
-constexpr int MIX_SM_TABLE = 256;   // home classes by %smid (modulo this size)
-
-struct MixClass {
-  int32_t *queue;   // [total * max_half] the class's frame-half list: +-(list entry + 1) once filled
-  int32_t *ctrl;    // [4] slots reserved, word tickets, frames finished (or parked); [3] unused
-  int64_t total;    // frames of the class (0: no such class in the launch)
-  int32_t slot_n;   // word tickets per list slot: the largest n of the class's codes
-  int32_t npl;      // lane layout of the class
-  int32_t g0, g1;   // its groups: groups[g0 .. g1), ordered by `first`
-  int32_t single;   // 1: one group, whose parameters are also passed as the kernel's own parameter
-};
-
-// Passed by value as a __grid_constant__ kernel parameter.  A class with a
-// single group reads that group's parameters from a separate by-value kernel
-// parameter of its slot (read like any kernel parameter); a class of several
-// codes indexes groups[] at run time.
-struct MixArgs {
-  MixGroup groups[MIX_MAX_GROUPS];
-  MixClass cls[MIX_MAX_CLASSES];  // by slot
-  int32_t ngroups;
-  int32_t present;                // bit s: class slot s has frames
-  int32_t max_half;        // the largest 2 * max iterations
-  int32_t wstride;         // shared bytes per warp: the largest per-warp layout of the classes
-  int32_t dpbytes;         // the block's remaining-mass area: the largest of the groups
-  int32_t max_spin;
-  int32_t *err;            // [1] launch-wide error word (a group's a.ctrl + 3)
-  unsigned char *dp_area;  // the blocks' remaining-mass areas in global memory (as ProductArgs)
-  int32_t dp_stride, dp_blocks;
-  int32_t *xf_count;
-  unsigned long long *wsum;
-  uint8_t home[MIX_SM_TABLE];  // class whose code path the warps of SM s run first
 };
 
 template <int NPL, class SYN>
@@ -147,12 +98,7 @@ template <int NPL, class SYN, bool GEN>
 cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, const SisoParams &P,
                                       const ProductArgs &a, cudaStream_t s);
 
-// Mixed form: init kernel and the persistent mixed kernel (MINB 6 or 8 blocks per SM).
-template <class SYN, int MINB>
-cudaError_t launch_product_mixed(const MixArgs &m, int epoch_halves, cudaStream_t s);
-
 // shared-memory layout sizes of a code: per warp, and the block's remaining-mass area
-int warp_area_bytes(int npl, int syn_bytes);
 int dp_area_bytes(int npl, int syn_bytes, int jmax);
 // bytes of one block's slice of a global remaining-mass region
 int dp_slice_bytes(int npl, int syn_bytes, int jmax);

@@ -176,7 +176,7 @@ size_t carve(Pool &p, int max_iter, char *mem) {
   p.queries = (int64_t *)take(S * 8);
   p.par_queries = (int64_t *)take(S * 8);
   p.queue = (int32_t *)take(S * 2 * max_iter * 4);
-  p.ctrl = (int32_t *)take(16);
+  p.ctrl = (int32_t *)take(32);
   p.dp_area = (unsigned char *)take((size_t)p.dp_blocks * p.dp_stride);
   return off;
 }

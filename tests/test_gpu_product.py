@@ -223,12 +223,17 @@ def test_mixed_form_equals_each_code_alone(env):
         for key in ("bits", "half_iters", "status", "queries"):
             np.testing.assert_array_equal(o[key].cpu().numpy(), r[key], err_msg=f"{name} {key}")
     assert outs[0]["status"][5].item() == 2
-    assert info["launches"] == 2 and info["timing_ms"] > 0
-    # groups needing 32-bit and 64-bit syndromes cannot share a launch
-    H = np.random.default_rng(5).integers(0, 2, (40, 64)).astype(np.uint8)
+    assert info["launches"] == 1 and info["timing_ms"] > 0  # one graph launch
+    # a code with 40 checks (64-bit syndromes) shares the launch with 32-bit ones
+    code40 = ebch("ebch_64_57")
+    H = np.concatenate([code40.H, np.random.default_rng(5).integers(0, 2, (33, 64)).astype(np.uint8)])
     wide = sg.Code(H, even=False)
-    with pytest.raises(sg.SograndError):
-        sg.product_decode_mixed([groups[0], (wide, torch.zeros((1, 64, 64), device="cuda"))])
+    lw = torch.from_numpy(awgn_frames(code40, 6, 6.0, seed=880)[2]).cuda()
+    r = sg.product_decode(wide, lw, L=4, query_cap=10**4, alpha=0.5, max_iter=2, persistent=True)
+    outs2, _ = sg.product_decode_mixed([groups[0], (wide, lw)], L=4, query_cap=10**4, alpha=0.5, max_iter=2)
+    torch.cuda.synchronize()
+    for key in ("bits", "half_iters", "status", "queries"):
+        np.testing.assert_array_equal(outs2[1][key].cpu().numpy(), r[key].cpu().numpy(), err_msg=f"40 checks {key}")
     wide.close()
     for c in codes:
         c.close()
