@@ -380,7 +380,7 @@ def other_configs(sg, torch, cores, reps=2):
     c4 = {"workload": f"{total} frames, eBCH(32,26)^2 : (64,51)^2 : (128,120)^2 = 4:2:1 "
                       f"({counts[0]} + {counts[1]} + {counts[2]}), Eb/N0 uniform 2.5..4.0 dB per frame, L=4, "
                       "cap 1e4, alpha 0.5, max 20 iterations", "frames": total, "info_bits": info,
-          "schedules": {nm: c.schedule() for nm, (c, _) in zip(names, groups)}}
+          "schedules": {nm: (c.schedule(), "global" if c.dp_area() else "shared") for nm, (c, _) in zip(names, groups)}}
     box = {}
     ms = _events_ms(torch, lambda: box.update(o=sg.product_decode_mixed(groups, stats=False, **kw)[0]), reps)
     c4["mixed"] = {"ms": ms, "bits_per_s": info / (ms / 1000), "launches": 2,
@@ -647,7 +647,8 @@ def main():
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": clk, "gpu_launches": launches,
                 "queries_per_s": world * qtot / (ms / 1000), "xf_words": int(out["xf_words"].item()),
                 "quality": quality, "serving": serving, "other_configs": others,
-                "schedule": {"blocks_per_sm": sched, "tuned_on": f"{min(F, 10_000)} frames",
+                "schedule": {"blocks_per_sm": sched, "remaining_mass_area": ("global" if c.dp_area() else "shared"),
+                             "tuned_on": f"{min(F, 10_000)} frames",
                              "sample_ms": {"6": sched_ms[0], "8": sched_ms[1]}},
                 "form": ("persistent (one kernel per decode, device-side frame queue)" if main_persistent
                          else "plain (one launch per half iteration)")}

@@ -275,12 +275,27 @@ int gldpc_decode(sogrand_code *code, int64_t n_frames, const float *llr_ch, int 
 int sogrand_code_schedule(sogrand_code *code, int minb, int *current);
 
 /*
+ * Where the batched forms keep each block's remaining-mass area (the exact
+ * positive-sum fallback of Sec. IV's remaining mass, used by about 1% of
+ * component decodings or fewer): 0 in shared memory, 1 in global memory,
+ * which leaves the SM's on-chip memory to L1 (faster for long codes and codes
+ * with many checks).  The default until tuned: shared for n <= 64 and
+ * n - k <= 8, else global; sogrand_code_tune measures both.
+ *   where    -1 (query only), 0 or 1
+ *   current  HOST out (may be NULL): the placement in force
+ * Not to be changed while a decode of this code is in flight.  Errors: EINVAL.
+ */
+int sogrand_code_dp_area(sogrand_code *code, int where, int *current);
+
+/*
  * Autotuner: decodes a sample of frames (device [n_frames][n][n] LLRs, with
  * the decode parameters of the intended workload) with the batched form
- * under each schedule, twice each (the first run warms caches), and keeps the
- * faster for this code.  Synchronous on `stream`; writes no caller buffer
- * but `chosen` (HOST, may be NULL: 6 or 8) and ms_out (HOST [2] or NULL: the
- * timed runs for 6 and 8 blocks per SM).  Errors: as
+ * under each schedule (6 or 8 blocks per SM, each with the remaining-mass
+ * area in shared and in global memory), twice each (the first run warms
+ * caches), and keeps the fastest for this code.  Synchronous on `stream`;
+ * writes no caller buffer but `chosen` (HOST, may be NULL: 6 or 8) and ms_out
+ * (HOST [2] or NULL: the better timed run for 6 and for 8 blocks per SM); the
+ * chosen placement is read with sogrand_code_dp_area.  Errors: as
  * product_decode_persistent; EINVAL also for n_frames < 1.
  */
 int sogrand_code_tune(sogrand_code *code, int64_t n_frames, const float *llr_ch, int L, int64_t query_cap, float thr,

@@ -26,6 +26,7 @@ struct sogrand_code {
   sg::DevOrder ord{};
   int jmax = 1;
   int minb = 6;  // schedule: resident blocks per SM (6 or 8), see sogrand_code_tune
+  int dp_global = 1;  // schedule: the batched forms keep the remaining-mass area in global memory
   int64_t tab_cap = 0;
   int64_t tab_bytes = 0;
   std::mutex mu;
@@ -254,6 +255,7 @@ sg::DevCode dev_code(const sogrand_code *c) {
   d.ord = c->ord;
   d.jmax = c->jmax;
   d.minb = c->minb;
+  d.dp_global = c->dp_global;
   return d;
 }
 
@@ -402,6 +404,7 @@ cudaError_t launch_persistent_for(const sogrand_code *c, const sg::SisoParams &P
 }
 sg::SisoParams siso_params_of(int L, int64_t cap, float thr) { return siso_params(L, cap, thr); }
 int32_t queue_wait_us() { return (int32_t)g_queue_wait_us.load(); }
+int code_dp_global(const sogrand_code *c) { return c->dp_global; }
 int dp_slice(const sogrand_code *c) {
   return sg::dp_slice_bytes(c->n <= 32 ? 1 : (c->n <= 64 ? 2 : 4), c->m > 32 ? 8 : 4, c->jmax);
 }
@@ -463,6 +466,8 @@ int sogrand_code_create(int n, int k, const uint8_t *H, int even, sogrand_code *
   // default schedule until tuned: 8 blocks per SM (64 registers) for short
   // codes with few checks, else 6 (80 registers)
   c->minb = (n <= 64 && m <= 8) ? 8 : 6;
+  // and the remaining-mass area in global memory for the others (they gain L1)
+  c->dp_global = (n <= 64 && m <= 8) ? 0 : 1;
   c->log_phi = (float)(log_pow2m1(k) - log_pow2m1(even ? n - 1 : n));
   cudaGetDevice(&c->device);
   std::vector<uint64_t> hcol(n, 0), hrow((size_t)m * c->nm, 0);
@@ -769,7 +774,8 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   a.status = status ? status : st_s;
   a.max_spin = (int32_t)g_queue_wait_us.load();  // back-off without any work before giving up
   // the blocks' remaining-mass areas: the region that follows the scratch
-  a.dp_area = (unsigned char *)(mem + al256(persistent_scratch_bytes(F, nr, nc, nm, max_iter)));
+  // (or shared memory, as the code's schedule says)
+  a.dp_area = c->dp_global ? (unsigned char *)(mem + al256(persistent_scratch_bytes(F, nr, nc, nm, max_iter))) : nullptr;
   a.dp_stride = dp_slice_of(c, cc);
   a.dp_blocks = sgi::sm_count_of_device() * MAX_BLOCKS_PER_SM;
   a.xf_count = xf;
@@ -863,6 +869,13 @@ int sogrand_code_schedule(sogrand_code *c, int minb, int *current) {
   return SOGRAND_OK;
 }
 
+int sogrand_code_dp_area(sogrand_code *c, int where, int *current) {
+  if (!c || where < -1 || where > 1) return SOGRAND_EINVAL;
+  if (where >= 0) c->dp_global = where;
+  if (current) *current = c->dp_global;
+  return SOGRAND_OK;
+}
+
 int sogrand_code_tune(sogrand_code *c, int64_t F, const float *llr_ch, int L, int64_t cap, float thr, float alpha,
                       int max_iter, int *chosen, float *ms_out, void *stream) {
   int rc = persistent_check(c, c, F, L, cap, thr, alpha, max_iter);
@@ -872,12 +885,14 @@ int sogrand_code_tune(sogrand_code *c, int64_t F, const float *llr_ch, int L, in
   const size_t nb = ((size_t)c->n * c->n + 7) / 8;
   char *bits = nullptr;
   if (scratch_alloc(&bits, al256((size_t)F * nb), s) != cudaSuccess) return SOGRAND_ENOMEM;
-  const int cand[2] = {6, 8};
+  // every (blocks per SM, remaining-mass area) pair
+  const int cand[4] = {6, 6, 8, 8}, cdp[4] = {0, 1, 0, 1};
   float best = 0.f, ms[2] = {0.f, 0.f};
-  int pick = c->minb;
-  const int keep = c->minb;
-  for (int i = 0; i < 2 && rc == SOGRAND_OK; i++) {
+  int pick = c->minb, pick_dp = c->dp_global;
+  const int keep = c->minb, keep_dp = c->dp_global;
+  for (int i = 0; i < 4 && rc == SOGRAND_OK; i++) {
     c->minb = cand[i];
+    c->dp_global = cdp[i];
     float t = 0.f;
     for (int rep = 0; rep < 2 && rc == SOGRAND_OK; rep++) {  // the first run warms caches and the pool
       float tm[2] = {0.f, 0.f};
@@ -886,13 +901,16 @@ int sogrand_code_tune(sogrand_code *c, int64_t F, const float *llr_ch, int L, in
                                      nullptr, nullptr, &st, stream);
       t = tm[0];
     }
-    ms[i] = t;
+    const int j = i / 2;
+    if (i % 2 == 0 || t < ms[j]) ms[j] = t;  // the better placement for this block count
     if (rc == SOGRAND_OK && (i == 0 || t < best)) {
       best = t;
       pick = cand[i];
+      pick_dp = cdp[i];
     }
   }
   c->minb = rc == SOGRAND_OK ? pick : keep;
+  c->dp_global = rc == SOGRAND_OK ? pick_dp : keep_dp;
   if (cudaFreeAsync(bits, s) != cudaSuccess && rc == SOGRAND_OK) rc = SOGRAND_ECUDA;
   if (rc == SOGRAND_OK) {
     if (chosen) *chosen = pick;

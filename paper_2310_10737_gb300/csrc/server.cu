@@ -44,6 +44,7 @@ int sm_count_of_device();
 sg::SisoParams siso_params_of(int L, int64_t cap, float thr);
 int32_t queue_wait_us();
 int dp_slice(const sogrand_code *c);
+int code_dp_global(const sogrand_code *c);
 }  // namespace sgi
 
 namespace {
@@ -317,7 +318,7 @@ cudaError_t launch(sogrand_server *sv, Pool &p, int64_t total_words) {
   a.bad = p.bad;
   a.ctrl = p.ctrl;
   a.max_spin = sgi::queue_wait_us();
-  a.dp_area = p.dp_area;
+  a.dp_area = sgi::code_dp_global(p.code) ? p.dp_area : nullptr;
   a.dp_stride = p.dp_stride;
   a.dp_blocks = p.dp_blocks;
   a.half_stop = p.half_stop;

@@ -38,6 +38,7 @@ struct DevCode {
   DevOrder ord;
   int32_t jmax;          // largest stored cost + 2 (bounds the remaining-mass DP)
   int32_t minb;          // schedule: resident blocks per SM the kernels are compiled for (6 or 8)
+  int32_t dp_global;     // schedule: the batched forms keep the remaining-mass area in global memory
 };
 
 struct SisoParams {

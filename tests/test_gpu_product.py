@@ -241,8 +241,9 @@ def test_mixed_form_equals_each_code_alone(env):
 
 @pytest.mark.parametrize("name", ["ebch_64_57", "ebch_64_51", "ebch_32_26"])
 def test_schedules_give_identical_results_and_tuner_picks_one(env, name):
-    """The two compiled schedules (6 or 8 resident blocks per SM) run the same
-    arithmetic; the autotuner keeps the faster one for the code."""
+    """The two compiled schedules (6 or 8 resident blocks per SM), with the
+    remaining-mass area in shared or in global memory, run the same
+    arithmetic; the autotuner keeps the fastest one for the code."""
     torch, sg = env
     code = ebch(name)
     U, X, lch = awgn_frames(code, 400, 2.75, seed=900)
@@ -251,18 +252,22 @@ def test_schedules_give_identical_results_and_tuner_picks_one(env, name):
     outs = []
     for minb in (6, 8):
         assert c.schedule(minb) == minb
-        for persistent in (True, False):
-            o = sg.product_decode(c, d, L=4, query_cap=10**4, alpha=0.5, max_iter=10, persistent=persistent)
-            torch.cuda.synchronize()
-            outs.append({k: v.cpu().numpy() for k, v in o.items() if hasattr(v, "cpu")})
+        for where in (0, 1):
+            assert c.dp_area(where) == where
+            for persistent in (True, False):
+                o = sg.product_decode(c, d, L=4, query_cap=10**4, alpha=0.5, max_iter=10, persistent=persistent)
+                torch.cuda.synchronize()
+                outs.append({k: v.cpu().numpy() for k, v in o.items() if hasattr(v, "cpu")})
     for o in outs[1:]:
         for key in ("bits", "half_iters", "status", "queries", "weight_sum"):
             np.testing.assert_array_equal(o[key], outs[0][key], err_msg=key)
     chosen, ms = c.tune(d, max_iter=10)
-    assert chosen in (6, 8) and c.schedule() == chosen and min(ms) > 0
+    assert chosen in (6, 8) and c.schedule() == chosen and min(ms) > 0 and c.dp_area() in (0, 1)
     assert ms[(6, 8).index(chosen)] == min(ms)
     with pytest.raises(sg.SograndError):
         c.schedule(7)
+    with pytest.raises(sg.SograndError):
+        c.dp_area(2)
     c.close()
 
 
