@@ -15,7 +15,8 @@
 // ties fall to the lower index) and the H columns are permuted into rank order
 // in shared memory.  The query order depends only on (n, c, parity class), so
 // it is read from a flattened table: every chunk of 32 consecutive queries is
-// one coalesced 512-byte load, lane j takes query q0 + j, XORs its pattern's
+// one coalesced 512-byte copy (cp.async into the warp's shared slots, issued
+// while the previous chunk is tested), lane j takes query q0 + j, XORs its pattern's
 // H columns into the syndrome of y and reports a hit; __ballot_sync + __ffs
 // keep the hits in query order, so list, stop point and query count are those
 // of a sequential decoder.
@@ -237,7 +238,8 @@ struct Layout {
   // carveout of the 8-block schedule up a step and shrank L1 by a quarter.)
   static constexpr int o_lam = o_w + 32;
   static_assert(32 + 4 * NT + 4 * (NPL + 1) <= 8 * NT * NM, "lambda and the word head fit in the frame-check area");
-  static constexpr int warp_bytes = align16(o_w + 8 * NT * NM);
+  static constexpr int o_pf = align16(o_w + 8 * NT * NM);             // uint4[32] the next chunk of order entries
+  static constexpr int warp_bytes = o_pf + 16 * 32;
   // block area (sized for the 8-byte XF policy): sfac[NT+1], fu[NT+1], fb[NT+1], ek[J] (float), he[J], ho[J]
   static __host__ __device__ int dp_bytes(int jm) { return align16(24 * (NT + 1) + 20 * jm + 32); }
   // a block of WARPS_PER_BLOCK warps: their areas, the tail and the remaining-mass area
@@ -266,6 +268,7 @@ struct Scratch {
   __device__ float *lp() const { return reinterpret_cast<float *>(base + LY::o_lp); }
   __device__ float *wl() const { return reinterpret_cast<float *>(base + LY::o_wl); }
   __device__ uint8_t *perm() const { return base + LY::o_perm; }
+  __device__ uint4 *pf() const { return reinterpret_cast<uint4 *>(base + LY::o_pf); }
   __device__ uint64_t *W() const { return reinterpret_cast<uint64_t *>(base + LY::o_w); }
   // lambda by bit, kept here during the search and read back (volatile) for
   // the soft output, so that it holds no registers while the search runs
@@ -1114,6 +1117,13 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   bool have_lr2 = false;
   int wacc = 0;       // this lane's share of the summed pattern weights
   DF tmass = {0.f, 0.f};  // this lane's share of the queried mass (nonzero patterns)
+  // each lane's entry of the next chunk is copied into its 16-byte slot of the
+  // warp's shared area while the current chunk is tested (cp.async: no
+  // registers held, the L2 latency overlaps the chunk's work)
+  const unsigned pf_addr = (unsigned)__cvta_generic_to_shared(sc.pf() + lane);
+  if (lane < qlim)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(pf_addr), "l"(O.ent + tb + lane) : "memory");
+  asm volatile("cp.async.commit_group;" ::: "memory");
   for (;;) {
     const int lim = min(32, qlim - q);
     if (lim <= 0) break;
@@ -1121,7 +1131,11 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     nchunks++;
 #endif
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
-    if (lane < lim) e = __ldg(O.ent + tb + q + lane);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    if (lane < lim) e = sc.pf()[lane];  // after the wait (a compiler barrier): this lane's own slot
+    if (q + 32 + lane < qlim)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(pf_addr), "l"(O.ent + tb + q + 32 + lane) : "memory");
+    asm volatile("cp.async.commit_group;" ::: "memory");
     const int w = e.x & 0xff;
     const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
     DF mass;
