@@ -1177,6 +1177,9 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     df_acc(tmass, mass);
     q += lim;
   }
+  // a copy for a chunk that was not needed may still be in flight: wait for
+  // it, so that it cannot land in the slot after the next word's first copy
+  asm volatile("cp.async.wait_all;" ::: "memory");
   // the whole parity class has been queried: nothing remains
   const bool exhausted = q >= tc && tc == O.class_size;
   __syncwarp();
