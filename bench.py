@@ -44,11 +44,11 @@ METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 # capture of a 10,000-frame decode of this workload (traffic grows with the
 # frame count at a fixed Eb/N0 mix), valid only for the kernel sources whose
 # digest is recorded with it: `traffic` is null once they change.
-TRAFFIC = {"csrc_digest": "f0f9405f92bf15e4a19384fbc0010a3346e299c0335304288bed724893842f6e",
-           "bytes_per_frame": 307253.2,
+TRAFFIC = {"csrc_digest": "c4ff6b7d49cfd2a41a7ffa5252ad421fe9ffd26e53ef33724062b87e272b676d",
+           "bytes_per_frame": 269476.2,
            "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md",
            # pipe activity of the same capture (percent of peak sustained over active cycles)
-           "ncu": {"issue_active_pct": 49.2, "alu_pipe_pct": 33.9, "fma_pipe_pct": 16.2,
+           "ncu": {"issue_active_pct": 56.9, "alu_pipe_pct": 42.8, "fma_pipe_pct": 18.2,
                    "tensor_pipe_pct": 0.0, "dram_throughput_pct": 1.1}}
 
 
