@@ -1082,12 +1082,18 @@ __device__ __noinline__ LoopOut query_loop_plain(const Scratch<NPL, SYN> sc, con
                                                  const uint4 *ent, int qlim, int L, int lane) {
   int q = 0, nhit = 0, wacc = 0;
   DF tmass = {0.f, 0.f};
+#ifdef SG_PHASE_PROFILE
+  int nchunks = 0;
+#endif
   const unsigned pf_addr = (unsigned)__cvta_generic_to_shared(sc.pf() + lane);
   if (lane < qlim) asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(pf_addr), "l"(ent + lane) : "memory");
   asm volatile("cp.async.commit_group;" ::: "memory");
   for (;;) {
     const int lim = min(32, qlim - q);
     if (lim <= 0) break;
+#ifdef SG_PHASE_PROFILE
+    nchunks++;
+#endif
     uint4 e = make_uint4(0u, 0u, 0u, 0u);
     asm volatile("cp.async.wait_all;" ::: "memory");
     if (lane < lim) e = sc.pf()[lane];
@@ -1124,6 +1130,9 @@ __device__ __noinline__ LoopOut query_loop_plain(const Scratch<NPL, SYN> sc, con
     q += lim;
   }
   asm volatile("cp.async.wait_all;" ::: "memory");
+#ifdef SG_PHASE_PROFILE
+  if (lane == 0) SG_PROF(5, nchunks);
+#endif
   return LoopOut{q, nhit, wacc, tmass};
 }
 
@@ -1189,66 +1198,66 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
     wacc = lo.wacc;
     tmass = lo.tmass;
   } else {  // with the threshold rule checked at every new list word
-  const unsigned pf_addr = (unsigned)__cvta_generic_to_shared(sc.pf() + lane);
-  if (lane < qlim)
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(pf_addr), "l"(O.ent + tb + lane) : "memory");
-  asm volatile("cp.async.commit_group;" ::: "memory");
-  for (;;) {
-    const int lim = min(32, qlim - q);
-    if (lim <= 0) break;
-#ifdef SG_PHASE_PROFILE
-    nchunks++;
-#endif
-    uint4 e = make_uint4(0u, 0u, 0u, 0u);
-    asm volatile("cp.async.wait_all;" ::: "memory");
-    if (lane < lim) e = sc.pf()[lane];  // after the wait (a compiler barrier): this lane's own slot
-    if (q + 32 + lane < qlim)
-      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(pf_addr), "l"(O.ent + tb + q + 32 + lane) : "memory");
+    const unsigned pf_addr = (unsigned)__cvta_generic_to_shared(sc.pf() + lane);
+    if (lane < qlim)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(pf_addr), "l"(O.ent + tb + lane) : "memory");
     asm volatile("cp.async.commit_group;" ::: "memory");
-    const int w = e.x & 0xff;
-    const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
-    DF mass;
-    const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr(), mass) ^ h.s0;
-    const bool hit = lane < lim && s == 0;
-    unsigned hm = __ballot_sync(FULL, hit);
-    int stop_lane = -1;
-    while (hm) {
-      const int hl = __ffs(hm) - 1;
-      hm &= hm - 1;
-      record_hit<NPL, SYN>(sc, h, e, hl, nhit, lane);
-      nhit++;
-      if (nhit >= P.L) {
-        stop_lane = hl;
-        break;
-      }
-      if (P.thr > 0.f) {
-        DF part = tmass;
-        if (lane <= hl) df_acc(part, mass);
-        const DF tq = df_warp_sum(part);
-        const float r2 = remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q + hl, n, (int)sc.head_at(NPL), cls, lane, tq, flags);
-        if (thr_reached(sc, nhit, r2 * LN2_F + code.log_phi, P.thr)) {
+    for (;;) {
+      const int lim = min(32, qlim - q);
+      if (lim <= 0) break;
+#ifdef SG_PHASE_PROFILE
+      nchunks++;
+#endif
+      uint4 e = make_uint4(0u, 0u, 0u, 0u);
+      asm volatile("cp.async.wait_all;" ::: "memory");
+      if (lane < lim) e = sc.pf()[lane];  // after the wait (a compiler barrier): this lane's own slot
+      if (q + 32 + lane < qlim)
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(pf_addr), "l"(O.ent + tb + q + 32 + lane) : "memory");
+      asm volatile("cp.async.commit_group;" ::: "memory");
+      const int w = e.x & 0xff;
+      const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
+      DF mass;
+      const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr(), mass) ^ h.s0;
+      const bool hit = lane < lim && s == 0;
+      unsigned hm = __ballot_sync(FULL, hit);
+      int stop_lane = -1;
+      while (hm) {
+        const int hl = __ffs(hm) - 1;
+        hm &= hm - 1;
+        record_hit<NPL, SYN>(sc, h, e, hl, nhit, lane);
+        nhit++;
+        if (nhit >= P.L) {
           stop_lane = hl;
-          lr2 = r2;
-          have_lr2 = true;
           break;
         }
+        if (P.thr > 0.f) {
+          DF part = tmass;
+          if (lane <= hl) df_acc(part, mass);
+          const DF tq = df_warp_sum(part);
+          const float r2 = remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q + hl, n, (int)sc.head_at(NPL), cls, lane, tq, flags);
+          if (thr_reached(sc, nhit, r2 * LN2_F + code.log_phi, P.thr)) {
+            stop_lane = hl;
+            lr2 = r2;
+            have_lr2 = true;
+            break;
+          }
+        }
       }
-    }
-    if (stop_lane >= 0) {
-      if (lane <= stop_lane) {
-        wacc += w;
-        df_acc(tmass, mass);
+      if (stop_lane >= 0) {
+        if (lane <= stop_lane) {
+          wacc += w;
+          df_acc(tmass, mass);
+        }
+        q += stop_lane + 1;
+        break;
       }
-      q += stop_lane + 1;
-      break;
+      wacc += w;  // lanes past lim hold an empty entry
+      df_acc(tmass, mass);
+      q += lim;
     }
-    wacc += w;  // lanes past lim hold an empty entry
-    df_acc(tmass, mass);
-    q += lim;
-  }
-  // a copy for a chunk that was not needed may still be in flight: wait for
-  // it, so that it cannot land in the slot after the next word's first copy
-  asm volatile("cp.async.wait_all;" ::: "memory");
+    // a copy for a chunk that was not needed may still be in flight: wait for
+    // it, so that it cannot land in the slot after the next word's first copy
+    asm volatile("cp.async.wait_all;" ::: "memory");
   }
   // the whole parity class has been queried: nothing remains
   const bool exhausted = q >= tc && tc == O.class_size;
