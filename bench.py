@@ -487,7 +487,7 @@ def main():
     log("inputs resident on the device, code tables built")
     # schedule autotuner (set-up, outside the timed region): blocks per SM on a 10,000-frame sample
     sched, sched_ms = c.tune(d_in[: min(F, 10_000)], L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER)
-    log(f"schedule: {sched} blocks/SM (sample ms at 6 / 8: {sched_ms[0]:.1f} / {sched_ms[1]:.1f})")
+    log(f"schedule: {sched} blocks/SM (sample ms at 7 / 8: {sched_ms[0]:.1f} / {sched_ms[1]:.1f})")
     n, k = code.n, code.k
     out = dict(bits=torch.empty((F, n * n // 8), dtype=torch.uint8, device=dev),
                half_iters=torch.empty(F, dtype=torch.int32, device=dev),

@@ -25,7 +25,7 @@ struct sogrand_code {
   void *d_tab = nullptr;
   sg::DevOrder ord{};
   int jmax = 1;
-  int minb = 6;  // schedule: resident blocks per SM (6 or 8), see sogrand_code_tune
+  int minb = 7;  // schedule: resident blocks per SM (7 or 8), see sogrand_code_tune
   int dp_global = 1;  // schedule: the batched forms keep the remaining-mass area in global memory
   int64_t tab_cap = 0;
   int64_t tab_bytes = 0;
@@ -463,9 +463,9 @@ int sogrand_code_create(int n, int k, const uint8_t *H, int even, sogrand_code *
   c->even = even;
   c->c_max = n;
   c->nm = (n + 63) / 64;
-  // default schedule until tuned: 8 blocks per SM (64 registers) for short
-  // codes with few checks, else 6 (80 registers)
-  c->minb = (n <= 64 && m <= 8) ? 8 : 6;
+  // default schedule until tuned: 8 blocks per SM (64 registers) for codes
+  // of up to 64 bits, else 7 (72 registers)
+  c->minb = n <= 64 ? 8 : 7;
   // and the remaining-mass area in global memory for the others (they gain L1)
   c->dp_global = (n <= 64 && m <= 8) ? 0 : 1;
   c->log_phi = (float)(log_pow2m1(k) - log_pow2m1(even ? n - 1 : n));
@@ -863,7 +863,7 @@ int gldpc_decode(sogrand_code *code, int64_t F, const float *llr_ch, int L, int6
 }
 
 int sogrand_code_schedule(sogrand_code *c, int minb, int *current) {
-  if (!c || (minb != 0 && minb != 6 && minb != 8)) return SOGRAND_EINVAL;
+  if (!c || (minb != 0 && minb != 7 && minb != 8)) return SOGRAND_EINVAL;
   if (minb) c->minb = minb;
   if (current) *current = c->minb;
   return SOGRAND_OK;
@@ -886,7 +886,7 @@ int sogrand_code_tune(sogrand_code *c, int64_t F, const float *llr_ch, int L, in
   char *bits = nullptr;
   if (scratch_alloc(&bits, al256((size_t)F * nb), s) != cudaSuccess) return SOGRAND_ENOMEM;
   // every (blocks per SM, remaining-mass area) pair
-  const int cand[4] = {6, 6, 8, 8}, cdp[4] = {0, 1, 0, 1};
+  const int cand[4] = {7, 7, 8, 8}, cdp[4] = {0, 1, 0, 1};
   float best = 0.f, ms[2] = {0.f, 0.f};
   int pick = c->minb, pick_dp = c->dp_global;
   const int keep = c->minb, keep_dp = c->dp_global;

@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const 
     float lapp[NPL];
     WordResult res;
     int used_xf = 0;
-    siso_word<NPL, SYN, MINB == 8>(code, P, sc, lam, lane, lapp, res, &used_xf);
+    siso_word<NPL, SYN>(code, P, sc, lam, lane, lapp, res, &used_xf);
     const bool empty = res.nhit == 0;
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
@@ -192,7 +192,7 @@ static_assert(sizeof(WordCtx) <= 32, "the word's lambda follows the context in t
 // and the second set of words may be wrapped diagonals (a.diag); otherwise
 // it is a square code.n x code.n frame with columns as the second set.
 // Returns the word's query count (-1: non-finite input).
-template <int NPL, class SYN, bool COHERENT, bool GEN, bool DP_CALL>
+template <int NPL, class SYN, bool COHERENT, bool GEN>
 __device__ __forceinline__ int product_word(const DevCode &code, const SisoParams &P, const ProductArgs &a,
                                             const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
@@ -225,7 +225,7 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     ctx->half = half;
   }
   __syncwarp();
-  siso_word<NPL, SYN, DP_CALL>(code, P, sc, lam, lane, lapp, res, &used_xf);
+  siso_word<NPL, SYN>(code, P, sc, lam, lane, lapp, res, &used_xf);
   bool rows2;
   {
     const volatile WordCtx *vc = ctx;
@@ -407,7 +407,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_half(const DevCode rowc, 
     const int32_t fs = __ldg(a.fstate + f);
     if (fs != F_RUN && fs != F_BAD_PENDING) continue;  // finished frames only: a flag raised during
                                                         // this half must not change which words run
-    const int q = product_word<NPL, SYN, false, GEN, MINB == 8>(code, P, a, sc, f, wd, half, lane);
+    const int q = product_word<NPL, SYN, false, GEN>(code, P, a, sc, f, wd, half, lane);
     if (lane == 0 && q < 0) atomicExch(a.fstate + f, (int32_t)F_BAD_PENDING);
   }
   tally_flush(sc.tally(), a.wsum, a.xf_count, lane);
@@ -615,7 +615,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
     if (lane == 0) reinterpret_cast<WordCtx *>(sc.W())->li = li;
-    const int q = product_word<NPL, SYN, true, GEN, MINB == 8>(code, P, a, sc, f, w, half, lane);
+    const int q = product_word<NPL, SYN, true, GEN>(code, P, a, sc, f, w, half, lane);
     {
       const volatile WordCtx *vc = reinterpret_cast<const volatile WordCtx *>(sc.W());
       f = vc->f;
@@ -708,7 +708,7 @@ template <int NPL, class SYN>
 cudaError_t launch_decode(const DevCode &code, const SisoParams &P, const DecodeArgs &a, cudaStream_t s) {
   if (a.n_words <= 0) return cudaSuccess;
   const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
-  auto kern = code.minb == 8 ? k_decode<NPL, SYN, 8> : k_decode<NPL, SYN, 6>;
+  auto kern = code.minb == 8 ? k_decode<NPL, SYN, 8> : k_decode<NPL, SYN, 7>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = grid_for(kern, smem, a.n_words);
@@ -734,12 +734,12 @@ cudaError_t launch_product_half(const DevCode &rowc, const DevCode &colc, const 
   const int64_t items = a.n_frames * ((half & 1) ? a.nc : a.nr);
   const int minb = rowc.minb;
   if (half & 1) {
-    auto kern = minb == 8 ? k_product_half<NPL, SYN, true, 8, GEN> : k_product_half<NPL, SYN, true, 6, GEN>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, true, 8, GEN> : k_product_half<NPL, SYN, true, 7, GEN>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
   } else {
-    auto kern = minb == 8 ? k_product_half<NPL, SYN, false, 8, GEN> : k_product_half<NPL, SYN, false, 6, GEN>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, false, 8, GEN> : k_product_half<NPL, SYN, false, 7, GEN>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
@@ -775,7 +775,7 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   // with a global remaining-mass region only the warps' areas are shared memory
   const int smem = a.dp_area ? WARPS_PER_BLOCK * Layout<NPL, SYN>::warp_bytes + TAIL_BYTES
                              : block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
-  auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8, GEN> : k_product_persistent<NPL, SYN, 6, GEN>;
+  auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8, GEN> : k_product_persistent<NPL, SYN, 7, GEN>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;

@@ -37,7 +37,7 @@ struct DevCode {
   const uint64_t *hrow;  // [m][nm] rows of H as bit masks over the n positions
   DevOrder ord;
   int32_t jmax;          // largest stored cost + 2 (bounds the remaining-mass DP)
-  int32_t minb;          // schedule: resident blocks per SM the kernels are compiled for (6 or 8)
+  int32_t minb;          // schedule: resident blocks per SM the kernels are compiled for (7 or 8)
   int32_t dp_global;     // schedule: the batched forms keep the remaining-mass area in global memory
 };
 

@@ -775,10 +775,13 @@ __device__ __noinline__ DF class_total_df(const Scratch<NPL, SYN> &sc, int n, in
 }
 
 // The unqueried patterns summed directly: the cost DP of remaining_scaled
-// under the block's lock.
+// under the block's lock.  Out of line: the DP runs for 0.04-0.9% of the
+// component words, and as a call it keeps the two call sites of
+// remaining_log2 short (1-1.5% faster than inline for eBCH(32,26), (64,51)
+// and (128,120) at 7 blocks per SM; within 1% for eBCH(64,57)).
 template <int NPL, class SYN>
-__device__ __forceinline__ float remaining_log2_dp(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc,
-                                                   int qs, int n, int c, int cls, int lane, int *used_xf) {
+__device__ __noinline__ float remaining_log2_dp(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc,
+                                                int qs, int n, int c, int cls, int lane, int *used_xf) {
 #ifdef SG_PHASE_PROFILE
   if (lane == 0) SG_PROF(6, 1);
 #endif
@@ -805,17 +808,6 @@ __device__ __forceinline__ float remaining_log2_dp(const Scratch<NPL, SYN> &sc, 
   return out;
 }
 
-// The same, as a call.  Out of line only in the 64-register schedule: there
-// it keeps the two inlined call sites of remaining_log2 short (eBCH(64,57),
-// which needs the DP for about 0.2% of its words: 3% faster); with 80
-// registers the call's register saves cost more than they save (eBCH(64,51)
-// and (128,120), which need it more often: 13% and 8% slower out of line).
-template <int NPL, class SYN>
-__device__ __noinline__ float remaining_log2_dp_call(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc,
-                                                     int qs, int n, int c, int cls, int lane, int *used_xf) {
-  return remaining_log2_dp<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, lane, used_xf);
-}
-
 // log2 of the remaining (unqueried) mass relative to p(0^n|r); warp-uniform.
 // *used_xf (if given) gets bit 0 when the extended-range sum was needed and
 // bit 1 when the block's remaining-mass area could not be locked.
@@ -826,7 +818,7 @@ __device__ __noinline__ float remaining_log2_dp_call(const Scratch<NPL, SYN> &sc
 // relative), in double-float when it is at least 2^-26 of them (rounding of a
 // few 2^-46 moves it by at most about 1e-5 relative).  Otherwise the
 // unqueried patterns are summed directly.
-template <int NPL, class SYN, bool DP_CALL>
+template <int NPL, class SYN>
 __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, int tb, int tc, int qs, int n, int c,
                                 int cls, int lane, DF tq, int *used_xf) {
   // class total of the nonzero patterns: prod_e (1 + y t_e) as (even - 1, odd)
@@ -872,7 +864,6 @@ __device__ float remaining_log2(const Scratch<NPL, SYN> &sc, const DevOrder &O, 
     if (!in_range && lane == 0) SG_PROF(15, 1);
 #endif
   }
-  if constexpr (DP_CALL) return remaining_log2_dp_call<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, lane, used_xf);
   return remaining_log2_dp<NPL, SYN>(sc, O, tb, tc, qs, n, c, cls, lane, used_xf);
 }
 
@@ -1143,7 +1134,7 @@ __device__ __noinline__ LoopOut query_loop_plain(const Scratch<NPL, SYN> sc, con
 // sc.lp() (log p(z)/p(0)) and sc.wl() (APP of each word).  *flags (if given)
 // collects the remaining-mass flags (bit 0: extended range; bit 1: the
 // block's remaining-mass area could not be locked).
-template <int NPL, class SYN, bool DP_CALL = false>
+template <int NPL, class SYN>
 __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratch<NPL, SYN> &sc,
                           const float (&lam)[NPL], int lane, float (&lapp)[NPL], WordResult &res,
                           int *flags = nullptr) {
@@ -1234,7 +1225,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
           DF part = tmass;
           if (lane <= hl) df_acc(part, mass);
           const DF tq = df_warp_sum(part);
-          const float r2 = remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q + hl, n, (int)sc.head_at(NPL), cls, lane, tq, flags);
+          const float r2 = remaining_log2<NPL, SYN>(sc, O, tb, tc, q + hl, n, (int)sc.head_at(NPL), cls, lane, tq, flags);
           if (thr_reached(sc, nhit, r2 * LN2_F + code.log_phi, P.thr)) {
             stop_lane = hl;
             lr2 = r2;
@@ -1269,7 +1260,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   // soft output (Corollary + eq. LLRi)
   if (!have_lr2)
     lr2 = (exhausted || P.forney) ? -CUDART_INF_F
-                    : remaining_log2<NPL, SYN, DP_CALL>(sc, O, tb, tc, q - 1, n, (int)sc.head_at(NPL), cls, lane, df_warp_sum(tmass),
+                    : remaining_log2<NPL, SYN>(sc, O, tb, tc, q - 1, n, (int)sc.head_at(NPL), cls, lane, df_warp_sum(tmass),
                                                flags);
 #ifdef SG_PHASE_PROFILE
   const long long t3 = clock64();
