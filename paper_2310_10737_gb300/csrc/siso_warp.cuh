@@ -425,22 +425,34 @@ __device__ __forceinline__ int ent_rank(const uint4 &e) {
 // p(0), the product of its ranks' factors, in double-float (0 for the zero
 // pattern).  The loop runs to the warp's largest weight; a shorter pattern's
 // extra bytes name the neutral record hr[n] (H column 0, factor 1: the XOR
-// and the products are exact no-ops).
+// and the products are exact no-ops).  Ranks go in pairs: both records are
+// loaded before either is used (two shared-memory loads in flight, half the
+// branches), and the pair's second rank past the weight is the neutral
+// record (2-3% faster than one rank at a time; fours were slower).
 template <class SYN>
 __device__ __forceinline__ SYN ent_syndrome(const uint4 &e, int w, int wmax, const RankRec<SYN> *hr, DF &mass) {
   SYN s = 0;
   float mh = 1.f, ml = 0.f;
-#define SG_R(K)                                    \
-  if (K < wmax) {                                  \
-    const RankRec<SYN> v = hr[ent_rank<K>(e)];     \
-    s ^= v.h;                                      \
-    const float p = __fmul_rn(mh, v.t);            \
-    ml = fmaf(ml, v.t, fmaf(mh, v.t, -p));         \
-    mh = p;                                        \
+  const auto mul = [&](float t) {
+    const float p = __fmul_rn(mh, t);
+    ml = fmaf(ml, t, fmaf(mh, t, -p));
+    mh = p;
+  };
+#define SG_R2(K)                                       \
+  if (K < wmax) {                                      \
+    const RankRec<SYN> v0 = hr[ent_rank<K>(e)];        \
+    const RankRec<SYN> v1 = hr[ent_rank<K + 1>(e)];    \
+    s ^= v0.h ^ v1.h;                                  \
+    mul(v0.t);                                         \
+    mul(v1.t);                                         \
   }
-  SG_R(0) SG_R(1) SG_R(2) SG_R(3) SG_R(4) SG_R(5) SG_R(6) SG_R(7)
-  SG_R(8) SG_R(9) SG_R(10) SG_R(11) SG_R(12) SG_R(13) SG_R(14)
-#undef SG_R
+  SG_R2(0) SG_R2(2) SG_R2(4) SG_R2(6) SG_R2(8) SG_R2(10) SG_R2(12)
+#undef SG_R2
+  if (14 < wmax) {
+    const RankRec<SYN> v = hr[ent_rank<14>(e)];
+    s ^= v.h;
+    mul(v.t);
+  }
   mass = w > 0 ? DF{mh, ml} : DF{0.f, 0.f};
   return s;
 }
