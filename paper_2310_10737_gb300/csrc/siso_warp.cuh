@@ -401,11 +401,12 @@ __device__ __forceinline__ int one_line_c(int64_t sy, int64_t sxy, int n, int c_
   int64_t num = sy * D - Nb * sx;
   int64_t top = 2 * num + (int64_t)n * Nb;
   if (top < 0) return 0;
-  // floor(top / den) clamped to c_max: an FP32 estimate corrected with exact
-  // integer products (the quotient that matters is at most c_max <= 128)
+  // floor(top / den) clamped to c_max: an FP32 estimate (the hardware
+  // reciprocal: a few ulp) corrected with exact integer products (the
+  // quotient that matters is at most c_max <= 128)
   const int64_t den = 2 * (int64_t)n * Nb;
   if (top >= (int64_t)(c_max + 1) * den) return c_max;
-  int64_t c = (int64_t)((float)top / (float)den);
+  int64_t c = (int64_t)__fdividef((float)top, (float)den);
   c = c < 0 ? 0 : (c > c_max ? c_max : c);
   while (c > 0 && c * den > top) c--;
   while (c < c_max && (c + 1) * den <= top) c++;
