@@ -264,11 +264,12 @@ int gldpc_decode(sogrand_code *code, int64_t n_frames, const float *llr_ch, int 
 
 /*
  * Schedule of a code's decoding kernels: the number of resident blocks per SM
- * (128 threads each) they are compiled for, 7 (72 registers a thread) or 8
- * (64 registers).  Which is faster depends on the code (register pressure of
- * its syndrome width and list) and is measured by sogrand_code_tune.  The
- * default until tuned: 8 for n <= 64, else 7.
- *   minb     0 (query only), 7 or 8
+ * (128 threads each) they are compiled for, 8 (64 registers a thread) or 12
+ * (40 registers).  Which is faster depends on the code (register pressure of
+ * its syndrome width and list against the latency the extra warps hide) and
+ * is measured by sogrand_code_tune.  The default until tuned: 12 for
+ * n <= 64, else 8.
+ *   minb     0 (query only), 8 or 12
  *   current  HOST out (may be NULL): the schedule in force
  * Not to be changed while a decode of this code is in flight.  Errors: EINVAL.
  */
@@ -290,11 +291,11 @@ int sogrand_code_dp_area(sogrand_code *code, int where, int *current);
 /*
  * Autotuner: decodes a sample of frames (device [n_frames][n][n] LLRs, with
  * the decode parameters of the intended workload) with the batched form
- * under each schedule (7 or 8 blocks per SM, each with the remaining-mass
+ * under each schedule (8 or 12 blocks per SM, each with the remaining-mass
  * area in shared and in global memory), twice each (the first run warms
  * caches), and keeps the fastest for this code.  Synchronous on `stream`;
- * writes no caller buffer but `chosen` (HOST, may be NULL: 7 or 8) and ms_out
- * (HOST [2] or NULL: the better timed run for 7 and for 8 blocks per SM); the
+ * writes no caller buffer but `chosen` (HOST, may be NULL: 8 or 12) and ms_out
+ * (HOST [2] or NULL: the better timed run for 8 and for 12 blocks per SM); the
  * chosen placement is read with sogrand_code_dp_area.  Errors: as
  * product_decode_persistent; EINVAL also for n_frames < 1.
  */

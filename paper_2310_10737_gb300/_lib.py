@@ -153,7 +153,7 @@ class Code:
         return cap.value, nb.value
 
     def schedule(self, minb: int = 0) -> int:
-        """Set (7 or 8) or query (0) the blocks per SM the decoding kernels run at."""
+        """Set (8 or 12) or query (0) the blocks per SM the decoding kernels run at."""
         cur = C.c_int(0)
         _check(load().sogrand_code_schedule(self.handle, int(minb), C.byref(cur)), "sogrand_code_schedule")
         return cur.value
@@ -166,7 +166,7 @@ class Code:
 
     def tune(self, llr_sample, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,
              max_iter: int = 20, stream=None):
-        """Autotune the schedule on a device sample [F, n, n]; returns (chosen, (ms at 7, ms at 8))."""
+        """Autotune the schedule on a device sample [F, n, n]; returns (chosen, (ms at 8, ms at 12))."""
         ch = C.c_int(0)
         ms = (C.c_float * 2)()
         _check(load().sogrand_code_tune(self.handle, int(llr_sample.shape[0]), _ptr(llr_sample), int(L),

@@ -25,7 +25,7 @@ struct sogrand_code {
   void *d_tab = nullptr;
   sg::DevOrder ord{};
   int jmax = 1;
-  int minb = 7;  // schedule: resident blocks per SM (7 or 8), see sogrand_code_tune
+  int minb = 12;  // schedule: resident blocks per SM (8 or 12), see sogrand_code_tune
   int dp_global = 1;  // schedule: the batched forms keep the remaining-mass area in global memory
   int64_t tab_cap = 0;
   int64_t tab_bytes = 0;
@@ -463,9 +463,9 @@ int sogrand_code_create(int n, int k, const uint8_t *H, int even, sogrand_code *
   c->even = even;
   c->c_max = n;
   c->nm = (n + 63) / 64;
-  // default schedule until tuned: 8 blocks per SM (64 registers) for codes
-  // of up to 64 bits, else 7 (72 registers)
-  c->minb = n <= 64 ? 8 : 7;
+  // default schedule until tuned: 12 blocks per SM (40 registers) for codes
+  // of up to 64 bits, else 8 (64 registers)
+  c->minb = n <= 64 ? 12 : 8;
   // and the remaining-mass area in global memory for the others (they gain L1)
   c->dp_global = (n <= 64 && m <= 8) ? 0 : 1;
   c->log_phi = (float)(log_pow2m1(k) - log_pow2m1(even ? n - 1 : n));
@@ -722,13 +722,12 @@ size_t persistent_scratch_bytes(int64_t F, int nr, int nc, int nm, int max_iter)
 
 // The global remaining-mass region of a persistent launch: one slice per
 // resident block (at most 8 blocks per SM in either schedule).
-constexpr int MAX_BLOCKS_PER_SM = 8;
 inline int npl_of_n(int n) { return n <= 32 ? 1 : (n <= 64 ? 2 : 4); }
 int dp_slice_of(const sogrand_code *rc, const sogrand_code *cc) {
   return sg::dp_slice_bytes(npl_of_n(rc->n), rc->m > 32 ? 8 : 4, std::max(rc->jmax, cc->jmax));
 }
 size_t dp_region_bytes(const sogrand_code *rc, const sogrand_code *cc) {
-  return al256((size_t)sgi::sm_count_of_device() * MAX_BLOCKS_PER_SM * dp_slice_of(rc, cc));
+  return al256((size_t)sgi::sm_count_of_device() * sg::MAX_BLOCKS_PER_SM * dp_slice_of(rc, cc));
 }
 
 // Queue set-up and the persistent kernel for F frames on stream s (nothing
@@ -777,7 +776,7 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   // (or shared memory, as the code's schedule says)
   a.dp_area = c->dp_global ? (unsigned char *)(mem + al256(persistent_scratch_bytes(F, nr, nc, nm, max_iter))) : nullptr;
   a.dp_stride = dp_slice_of(c, cc);
-  a.dp_blocks = sgi::sm_count_of_device() * MAX_BLOCKS_PER_SM;
+  a.dp_blocks = sgi::sm_count_of_device() * sg::MAX_BLOCKS_PER_SM;
   a.xf_count = xf;
   a.wsum = wsum;
   *err_dev = a.ctrl + 3;
@@ -863,7 +862,7 @@ int gldpc_decode(sogrand_code *code, int64_t F, const float *llr_ch, int L, int6
 }
 
 int sogrand_code_schedule(sogrand_code *c, int minb, int *current) {
-  if (!c || (minb != 0 && minb != 7 && minb != 8)) return SOGRAND_EINVAL;
+  if (!c || (minb != 0 && minb != 8 && minb != 12)) return SOGRAND_EINVAL;
   if (minb) c->minb = minb;
   if (current) *current = c->minb;
   return SOGRAND_OK;
@@ -886,7 +885,7 @@ int sogrand_code_tune(sogrand_code *c, int64_t F, const float *llr_ch, int L, in
   char *bits = nullptr;
   if (scratch_alloc(&bits, al256((size_t)F * nb), s) != cudaSuccess) return SOGRAND_ENOMEM;
   // every (blocks per SM, remaining-mass area) pair
-  const int cand[4] = {7, 7, 8, 8}, cdp[4] = {0, 1, 0, 1};
+  const int cand[4] = {8, 8, 12, 12}, cdp[4] = {0, 1, 0, 1};
   float best = 0.f, ms[2] = {0.f, 0.f};
   int pick = c->minb, pick_dp = c->dp_global;
   const int keep = c->minb, keep_dp = c->dp_global;

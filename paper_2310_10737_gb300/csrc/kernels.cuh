@@ -708,7 +708,7 @@ template <int NPL, class SYN>
 cudaError_t launch_decode(const DevCode &code, const SisoParams &P, const DecodeArgs &a, cudaStream_t s) {
   if (a.n_words <= 0) return cudaSuccess;
   const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
-  auto kern = code.minb == 8 ? k_decode<NPL, SYN, 8> : k_decode<NPL, SYN, 7>;
+  auto kern = code.minb == 8 ? k_decode<NPL, SYN, 8> : k_decode<NPL, SYN, 12>;
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = grid_for(kern, smem, a.n_words);
@@ -734,12 +734,12 @@ cudaError_t launch_product_half(const DevCode &rowc, const DevCode &colc, const 
   const int64_t items = a.n_frames * ((half & 1) ? a.nc : a.nr);
   const int minb = rowc.minb;
   if (half & 1) {
-    auto kern = minb == 8 ? k_product_half<NPL, SYN, true, 8, GEN> : k_product_half<NPL, SYN, true, 7, GEN>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, true, 8, GEN> : k_product_half<NPL, SYN, true, 12, GEN>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
   } else {
-    auto kern = minb == 8 ? k_product_half<NPL, SYN, false, 8, GEN> : k_product_half<NPL, SYN, false, 7, GEN>;
+    auto kern = minb == 8 ? k_product_half<NPL, SYN, false, 8, GEN> : k_product_half<NPL, SYN, false, 12, GEN>;
     cudaError_t e = set_smem(kern, smem);
     if (e != cudaSuccess) return e;
     kern<<<grid_for(kern, smem, items), TPB, smem, s>>>(rowc, colc, P, a, half);
@@ -775,7 +775,7 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   // with a global remaining-mass region only the warps' areas are shared memory
   const int smem = a.dp_area ? WARPS_PER_BLOCK * Layout<NPL, SYN>::warp_bytes + TAIL_BYTES
                              : block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
-  auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8, GEN> : k_product_persistent<NPL, SYN, 7, GEN>;
+  auto kern = rowc.minb == 8 ? k_product_persistent<NPL, SYN, 8, GEN> : k_product_persistent<NPL, SYN, 12, GEN>;
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;

@@ -326,7 +326,7 @@ cudaError_t launch(sogrand_server *sv, Pool &p, int64_t total_words) {
   a.epoch_halves = sv->epoch_halves;
   // the GPU is shared by the pools' concurrent launches in proportion to their words
   const int64_t words = F * p.n;
-  const int64_t full = (int64_t)sgi::sm_count_of_device() * 8;
+  const int64_t full = (int64_t)sgi::sm_count_of_device() * sg::MAX_BLOCKS_PER_SM;
   a.grid_cap = (int)std::max<int64_t>(full / 8, total_words > 0 ? (full * words + total_words - 1) / total_words : full);
   const sg::SisoParams P = sgi::siso_params_of(sv->L, sv->cap, sv->thr);
   if (e == cudaSuccess) e = sgi::launch_persistent_for(p.code, P, a, p.stream);
@@ -427,7 +427,7 @@ int sogrand_server_create(int n_codes, sogrand_code *const *codes, const int64_t
     p->nm = sgi::code_nm(codes[i]);
     p->slots = slots[i];
     p->dp_stride = sgi::dp_slice(codes[i]);
-    p->dp_blocks = sgi::sm_count_of_device() * 8;  // a slice for every block a launch can have resident
+    p->dp_blocks = sgi::sm_count_of_device() * sg::MAX_BLOCKS_PER_SM;  // a slice for every block a launch can have resident
     const size_t bytes = carve(*p, max_iter, nullptr);
     if (cudaMalloc(&p->mem, bytes) != cudaSuccess) {
       rc = SOGRAND_ENOMEM;

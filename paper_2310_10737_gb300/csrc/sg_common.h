@@ -12,6 +12,10 @@ constexpr int LMAX = 16;       // longest list a decode may request
 constexpr int WMAXT = 64;      // most Hamming weights a query-order table may reach
 constexpr int WENT = 15;       // most ranks one table entry holds
 constexpr int WARPS_PER_BLOCK = 4;
+// Schedules: the per-word kernels are compiled for 8 resident blocks per SM
+// (64 registers a thread) and for 12 (40 registers); a launch never has more
+// than MAX_BLOCKS_PER_SM blocks resident on an SM.
+constexpr int MAX_BLOCKS_PER_SM = 12;
 
 // Query order of one code, flattened per 1-line parameter c and parity class.
 // For every c in [0, c_max] and class (the parity of y for an even code, or
@@ -37,7 +41,7 @@ struct DevCode {
   const uint64_t *hrow;  // [m][nm] rows of H as bit masks over the n positions
   DevOrder ord;
   int32_t jmax;          // largest stored cost + 2 (bounds the remaining-mass DP)
-  int32_t minb;          // schedule: resident blocks per SM the kernels are compiled for (7 or 8)
+  int32_t minb;          // schedule: resident blocks per SM the kernels are compiled for (8 or 12)
   int32_t dp_global;     // schedule: the batched forms keep the remaining-mass area in global memory
 };
 
