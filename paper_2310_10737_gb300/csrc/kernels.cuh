@@ -529,6 +529,7 @@ __device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCod
                                                  uint64_t *W, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
   const int n = xc.n;  // words of this half
+  __syncwarp();  // after lane 0's acquire of the frame's word count: the other words' results
   __threadfence();
   const bool rows = (half & 1) != 0;
   const int hbw = GEN ? a.hbw : n;
