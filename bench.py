@@ -44,12 +44,12 @@ METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 # capture of a 10,000-frame decode of this workload (traffic grows with the
 # frame count at a fixed Eb/N0 mix), valid only for the kernel sources whose
 # digest is recorded with it: `traffic` is null once they change.
-TRAFFIC = {"csrc_digest": "5e0ce04e9e9b5479ad6ec83147accecddac6a57d7116e5f745fdf238c5aba0ef",
-           "bytes_per_frame": 271079.9,
+TRAFFIC = {"csrc_digest": "e3b54a1ca5775a7763d389247fec4bc41a0fb4dc8750415da0123f7eaba07a5d",
+           "bytes_per_frame": 278360.0,
            "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md",
            # pipe activity of the same capture (percent of peak sustained over active cycles)
-           "ncu": {"issue_active_pct": 60.7, "alu_pipe_pct": 44.6, "fma_pipe_pct": 20.3,
-                   "tensor_pipe_pct": 0.0, "dram_throughput_pct": 1.2}}
+           "ncu": {"issue_active_pct": 67.8, "alu_pipe_pct": 48.9, "fma_pipe_pct": 26.5,
+                   "tensor_pipe_pct": 0.0, "dram_throughput_pct": 1.5}}
 
 
 KERNEL_SOURCES = ("kernels.cuh", "launch.h", "sg_common.h", "siso_warp.cuh")  # what k_product_persistent compiles from
