@@ -320,11 +320,12 @@ typedef struct {
 /*
  * Mixed form of product decoding (Sec. VI turbo decoding of each frame, as
  * product_decode_persistent): frames of up to SOGRAND_MIX_MAX_GROUPS codes of
- * different lengths decoded by ONE launch of a CUDA graph that holds, on
- * parallel branches, the batched (persistent) decoder of every group, each
- * with its own frame-half list.  Each kernel has a full grid; as a kernel's
- * work runs out its surplus warps leave, and blocks of the other kernels take
- * the SMs, so one code's tail overlaps the next code's decoding (the paper
+ * different lengths decoded by ONE launch of a CUDA graph that holds the
+ * list set-up of every group and then the batched (persistent) decoder of
+ * every group, each with its own frame-half list, chained by programmatic
+ * dependent launches.  Each decoder has a full grid; as its work runs out
+ * its surplus warps leave, and the next group's decoder starts on the SMs
+ * they free, so one code's tail overlaps the next code's decoding (the paper
  * decodes one code at a time; this is a batching form of the same
  * computation).  Every frame's results equal those of
  * product_decode_persistent on that frame alone.  L, query_cap, thr, alpha

@@ -736,7 +736,8 @@ size_t dp_region_bytes(const sogrand_code *rc, const sogrand_code *cc) {
 cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t F, const float *llr_ch,
                                const sg::SisoParams &P, float alpha, int max_iter, uint8_t *bits, int32_t *half_iters,
                                uint8_t *status, int64_t *queries, int64_t *par_queries, unsigned long long *wsum,
-                               int32_t *xf, char *mem, cudaStream_t s, int32_t **err_dev, int diag = 0) {
+                               int32_t *xf, char *mem, cudaStream_t s, int32_t **err_dev, int diag = 0,
+                               int part = sg::PERSISTENT_ALL) {
   const int nr = c->n, nc = cc->n, nm = c->nm, hbw = std::max(nr, nc);
   char *p = mem;
   auto take = [&p](size_t bytes) {
@@ -783,8 +784,8 @@ cudaError_t persistent_enqueue(sogrand_code *c, const sogrand_code *cc, int64_t 
   sg::DevCode d = dev_code(c), dcol = dev_code(cc);
   const bool gen = cc != c || a.diag || a.nr != a.nc;  // not the square product of one code
   cudaError_t e = cudaSuccess;
-  SG_DISPATCH(c, e = (gen ? sg::launch_product_persistent<NPL, SYN, true>(d, dcol, P, a, s)
-                          : sg::launch_product_persistent<NPL, SYN, false>(d, dcol, P, a, s)));
+  SG_DISPATCH(c, e = (gen ? sg::launch_product_persistent<NPL, SYN, true>(d, dcol, P, a, s, part)
+                          : sg::launch_product_persistent<NPL, SYN, false>(d, dcol, P, a, s, part)));
   return e;
 }
 
@@ -1014,13 +1015,17 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
 }  // extern "C"
 
 namespace {
-// The mixed form as one CUDA graph: a persistent decoder kernel per group
-// (each the single-code batched kernel of its code, with its own frame-half
-// list) on parallel branches, launched with one cudaGraphLaunch.  Every
-// kernel gets a full grid; the hardware starts blocks of the next kernel as
-// blocks of an earlier one leave, and a kernel's warps leave as soon as its
-// unfinished frames cannot use them, so the tail of one code's decode
-// overlaps the start of the next and no SM idles while any code has work.
+// The mixed form as one CUDA graph, captured on one stream: the list set-up
+// of every group, then a persistent decoder kernel per group (each the
+// single-code batched kernel of its code, with its own frame-half list) in a
+// chain of programmatic dependent launches, launched with one cudaGraphLaunch.
+// A decoder's warps leave as soon as its unfinished frames cannot use them,
+// and once every block of it has begun to leave the next group's decoder may
+// start: its blocks take the SMs that the tail frees, so no SM idles while
+// any code has work, and two codes' kernels share an SM only in that tail
+// (on parallel branches they shared SMs throughout and competed for the
+// instruction cache, the kernel's first stall: about 1% slower than the
+// per-code launches in sequence).
 int mixed_graph_decode(int n_groups, const sogrand_frame_group *groups, int L, int64_t cap, float thr, float alpha,
                        int max_iter, product_decode_stats *stats, cudaStream_t s) {
   std::vector<int> live;
@@ -1034,42 +1039,28 @@ int mixed_graph_decode(int n_groups, const sogrand_frame_group *groups, int L, i
     off[x + 1] = off[x] + al256(persistent_scratch_bytes(G.n_frames, G.code->n, G.code->n, G.code->nm, max_iter)) +
                  dp_region_bytes(G.code, G.code);
   }
-  const size_t o_err = off[k];
   char *mem = nullptr;
-  if (scratch_alloc(&mem, o_err + 256, s) != cudaSuccess) return SOGRAND_ENOMEM;
-  int32_t *d_err = (int32_t *)(mem + o_err);  // one timeout flag per kernel
+  if (scratch_alloc(&mem, off[k] + 256, s) != cudaSuccess) return SOGRAND_ENOMEM;
   const sg::SisoParams P = siso_params(L, cap, thr);
-  std::vector<cudaStream_t> st(k, nullptr);
+  std::vector<int32_t *> err_dev(k, nullptr);  // each decoder's timeout flag
+  cudaStream_t cs = nullptr;
   std::vector<cudaEvent_t> ev;
-  cudaError_t e = cudaSuccess;
-  for (int x = 0; x < k && e == cudaSuccess; x++) e = cudaStreamCreateWithFlags(&st[x], cudaStreamNonBlocking);
-  auto event = [&ev, &e]() {
-    cudaEvent_t x = nullptr;
-    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&x, cudaEventDisableTiming);
-    if (x) ev.push_back(x);
-    return x;
-  };
+  cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  if (e == cudaSuccess) e = cudaStreamBeginCapture(st[0], cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
-    cudaEvent_t fork = event();
-    if (e == cudaSuccess) e = cudaEventRecord(fork, st[0]);
-    for (int x = 1; x < k && e == cudaSuccess; x++) e = cudaStreamWaitEvent(st[x], fork, 0);
-    for (int x = 0; x < k && e == cudaSuccess; x++) {
-      const sogrand_frame_group &G = groups[live[x]];
-      int32_t *err_x = nullptr;
-      e = persistent_enqueue(G.code, G.code, G.n_frames, G.llr_ch, P, alpha, max_iter, G.bits, G.half_iters, G.status,
-                             G.queries, nullptr, stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr,
-                             stats ? stats->xf_words : nullptr, mem + off[x], st[x], &err_x);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(d_err + x, err_x, sizeof(int32_t), cudaMemcpyDeviceToDevice, st[x]);
+    for (int pass = 0; pass < 2; pass++) {
+      for (int x = 0; x < k && e == cudaSuccess; x++) {
+        const sogrand_frame_group &G = groups[live[x]];
+        const int part = pass == 0 ? sg::PERSISTENT_INIT : (x == 0 ? sg::PERSISTENT_DECODE : sg::PERSISTENT_DECODE_PDL);
+        e = persistent_enqueue(G.code, G.code, G.n_frames, G.llr_ch, P, alpha, max_iter, G.bits, G.half_iters,
+                               G.status, G.queries, nullptr,
+                               stats ? reinterpret_cast<unsigned long long *>(stats->weight_sum) : nullptr,
+                               stats ? stats->xf_words : nullptr, mem + off[x], cs, &err_dev[x], 0, part);
+      }
     }
-    for (int x = 1; x < k && e == cudaSuccess; x++) {
-      cudaEvent_t join = event();
-      if (e == cudaSuccess) e = cudaEventRecord(join, st[x]);
-      if (e == cudaSuccess) e = cudaStreamWaitEvent(st[0], join, 0);
-    }
-    const cudaError_t ec = cudaStreamEndCapture(st[0], &graph);
+    const cudaError_t ec = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = ec;
   }
   if (e == cudaSuccess) e = cudaGraphInstantiate(&exec, graph, 0);
@@ -1084,8 +1075,10 @@ int mixed_graph_decode(int n_groups, const sogrand_frame_group *groups, int L, i
   if (e == cudaSuccess && timed) e = cudaEventRecord(t0, s);
   if (e == cudaSuccess) e = cudaGraphLaunch(exec, s);
   if (e == cudaSuccess && timed) e = cudaEventRecord(t1, s);
+  // the timeout flags, read after the whole graph (every decoder) has finished
   std::vector<int32_t> err(k, 0);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(err.data(), d_err, k * sizeof(int32_t), cudaMemcpyDeviceToHost, s);
+  for (int x = 0; x < k && e == cudaSuccess; x++)
+    e = cudaMemcpyAsync(&err[x], err_dev[x], sizeof(int32_t), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e == cudaSuccess && timed) {
     float ms = 0.f;
@@ -1096,8 +1089,7 @@ int mixed_graph_decode(int n_groups, const sogrand_frame_group *groups, int L, i
   if (exec) cudaGraphExecDestroy(exec);
   if (graph) cudaGraphDestroy(graph);
   for (cudaEvent_t x : ev) cudaEventDestroy(x);
-  for (cudaStream_t x : st)
-    if (x) cudaStreamDestroy(x);
+  if (cs) cudaStreamDestroy(cs);
   const cudaError_t e2 = cudaFreeAsync(mem, s);
   if (e != cudaSuccess || e2 != cudaSuccess) return SOGRAND_ECUDA;
   for (int32_t x : err)

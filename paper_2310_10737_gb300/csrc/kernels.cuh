@@ -614,7 +614,12 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
           atomicAdd(a.ctrl + 4, 1);
       }
     }
-    if (__shfl_sync(FULL, leave, 0)) break;
+    if (__shfl_sync(FULL, leave, 0)) {
+      // this block has begun to leave: a decoder launched as a programmatic
+      // dependent of this one may start (no effect otherwise)
+      asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+      break;
+    }
     int slot, w, f1;
     if (!sched_take(a.ctrl, a.ctrl + 3, a.queue, nslots, a.n_frames, slot_n, a.max_spin, lane, &slot, &w, &f1,
                     &waited))
@@ -790,11 +795,14 @@ cudaError_t launch_product_init(const DevCode &code, const ProductArgs &a, cudaS
 
 template <int NPL, class SYN, bool GEN>
 cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, const SisoParams &P,
-                                      const ProductArgs &a, cudaStream_t s) {
+                                      const ProductArgs &a, cudaStream_t s, int part) {
   if (a.n_frames <= 0) return cudaSuccess;
-  k_persistent_init<<<(int)std::min<int64_t>((a.n_frames + 255) / 256, 4096), 256, 0, s>>>(a);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
+  cudaError_t e = cudaSuccess;
+  if (part == PERSISTENT_ALL || part == PERSISTENT_INIT) {
+    k_persistent_init<<<(int)std::min<int64_t>((a.n_frames + 255) / 256, 4096), 256, 0, s>>>(a);
+    e = cudaGetLastError();
+    if (e != cudaSuccess || part == PERSISTENT_INIT) return e;
+  }
   // with a global remaining-mass region only the warps' areas are shared memory
   const int smem = a.dp_area ? WARPS_PER_BLOCK * Layout<NPL, SYN>::warp_bytes + TAIL_BYTES
                              : block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
@@ -812,6 +820,19 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   if (a.grid_cap > 0 && a.grid_cap < cap) cap = a.grid_cap;
   if (a.dp_area && a.dp_blocks < cap) cap = a.dp_blocks;  // one slice of the region per block
   const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(cap, want));
+  if (part == PERSISTENT_DECODE_PDL) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(TPB);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, rowc, colc, P, a);
+  }
   kern<<<grid, TPB, smem, s>>>(rowc, colc, P, a);
   return cudaGetLastError();
 }
@@ -828,7 +849,7 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   template cudaError_t launch_product_init<NPL, SYN>(const DevCode &, const ProductArgs &, cudaStream_t);           \
   template cudaError_t launch_product_persistent<NPL, SYN, false>(const DevCode &, const DevCode &,              \
                                                                   const SisoParams &, const ProductArgs &,       \
-                                                                  cudaStream_t);
+                                                                  cudaStream_t, int);
 
 // Launchers of the general geometry (two codes, or wrapped diagonals), in
 // translation units of their own so that they compile in parallel.
@@ -837,6 +858,6 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
                                                            const ProductArgs &, int, cudaStream_t);              \
   template cudaError_t launch_product_persistent<NPL, SYN, true>(const DevCode &, const DevCode &,               \
                                                                  const SisoParams &, const ProductArgs &,        \
-                                                                 cudaStream_t);
+                                                                 cudaStream_t, int);
 
 }  // namespace sg

@@ -94,9 +94,17 @@ template <int NPL, class SYN>
 cudaError_t launch_product_check(const DevCode &rowc, const DevCode &colc, const ProductArgs &a, int half,
                                  cudaStream_t s);
 
+// The batched form's two launches: the list set-up (k_persistent_init) and
+// the decoder.  `part` selects them: PERSISTENT_ALL both, PERSISTENT_INIT the
+// set-up only, PERSISTENT_DECODE the decoder only, PERSISTENT_DECODE_PDL the
+// decoder as a programmatic dependent launch: it may start once every block
+// of the previous kernel on the stream has begun to leave (the decoder's
+// warps signal that when they drain), so a chain of decoders overlaps only
+// at the tails.  The decoder reads nothing the previous kernel writes.
+enum PersistentPart { PERSISTENT_ALL = 0, PERSISTENT_INIT = 1, PERSISTENT_DECODE = 2, PERSISTENT_DECODE_PDL = 3 };
 template <int NPL, class SYN, bool GEN>
 cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, const SisoParams &P,
-                                      const ProductArgs &a, cudaStream_t s);
+                                      const ProductArgs &a, cudaStream_t s, int part = PERSISTENT_ALL);
 
 // shared-memory layout sizes of a code: per warp, and the block's remaining-mass area
 int dp_area_bytes(int npl, int syn_bytes, int jmax);
