@@ -312,7 +312,8 @@ def other_configs(sg, torch, cores, reps=2):
         (word w at point w mod 4), L in {1, 2, 4}, cap 1e5, one launch per code and L;
     C4  mixed batch: 200,000 frames of eBCH(32,26)^2, (64,51)^2, (128,120)^2 in 4:2:1,
         Eb/N0 uniform in 2.5..4.0 dB per frame, L=4, cap 1e4, 20 iterations: one mixed
-        launch vs the batched form per code vs the plain form per code."""
+        launch vs the batched form per code vs the plain form per code;
+    order_source: the order table against the lanes enumerating the order (order_source_ab)."""
     from workloads import awgn_frames, awgn_words, ebch
     res = {}
     dev = torch.device("cuda")
@@ -399,7 +400,59 @@ def other_configs(sg, torch, cores, reps=2):
     for c, _ in groups:
         c.close()
     res["C4"] = c4
+    res["order_source"] = order_source_ab(sg, torch, cores, reps)
     return res
+
+
+def order_source_ab(sg, torch, cores, reps):
+    """Where the query loop takes its patterns (sogrand_code_order_source): the
+    precomputed order table (the default) against the lanes enumerating the
+    1-line ORBGRAND order themselves (unranking distinct-part partitions), on
+    the first 20,000 frames of the headline workload (batched form, tuned
+    schedule) and on the C2 eBCH(64,57) words at L=4, cap 1e5.  Both sources
+    give identical outputs (checked here on the decoded bits and the query
+    counts)."""
+    from workloads import awgn_words, ebch
+    dev = torch.device("cuda")
+    code = ebch(CODE)
+    F = 20_000
+    _, _, lch = make_inputs(code, F, rank_seed(0), cores)
+    d = torch.from_numpy(lch).to(dev)
+    del lch
+    c = sg.Code.from_linear_code(code)
+    c.tune(d[:10_000], L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER)
+    kw = dict(L=L_LIST, query_cap=CAP, alpha=ALPHA, max_iter=MAX_ITER, persistent=True, stats=False)
+    r = {"workload": f"{F} frames of the headline workload (eBCH(64,57)^2, 2.5..4.0 dB), L=4, cap 1e4, "
+                     "20 iterations, batched form; C2 eBCH(64,57) 10^6 words, L=4, cap 1e5",
+         "schedule": [c.schedule(), "global" if c.dp_area() else "shared"]}
+    outs = {}
+    for name, src in (("table", 0), ("lanes", 1)):
+        c.order_source(src)
+        box = {}
+        ms = _events_ms(torch, lambda: box.update(o=sg.product_decode(c, d, **kw)), reps + 1)
+        outs[name] = (box["o"]["bits"].cpu().numpy(), box["o"]["queries"].cpu().numpy())
+        r[name] = {"ms": ms, "info_bits_per_s": F * code.k * code.k / (ms / 1000)}
+    c.order_source(0)
+    r["identical"] = bool((outs["table"][0] == outs["lanes"][0]).all() and (outs["table"][1] == outs["lanes"][1]).all())
+    c.close()
+    del d
+    W = 10**6
+    snr = np.array([2.0, 3.0, 4.0, 5.0])[np.arange(W) % 4]
+    _, _, lw = awgn_words(code, W, snr, seed=2, threads=cores)
+    c = sg.Code.from_linear_code(code)
+    c.reserve(10**5)
+    d = torch.from_numpy(lw).to(dev)
+    del lw
+    for name, src in (("c2_table", 0), ("c2_lanes", 1)):
+        c.order_source(src)
+        box = {}
+        ms = _events_ms(torch, lambda: box.update(o=sg.sogrand_decode(c, d, L=4, query_cap=10**5, lists=False)), reps)
+        q = int(box["o"]["queries"].sum())
+        r[name] = {"ms": ms, "words_per_s": W / (ms / 1000), "queries_per_s": q / (ms / 1000)}
+    c.close()
+    log(f"order source: table {r['table']['ms']:.1f} ms, lanes {r['lanes']['ms']:.1f} ms (identical: "
+        f"{r['identical']}); C2 L=4 table {r['c2_table']['ms']:.2f} ms, lanes {r['c2_lanes']['ms']:.2f} ms")
+    return r
 
 
 def cpu_oracle_rate(code, lch, threads):

@@ -289,6 +289,28 @@ int sogrand_code_schedule(sogrand_code *code, int minb, int *current);
 int sogrand_code_dp_area(sogrand_code *code, int where, int *current);
 
 /*
+ * Where the query loop takes its patterns (1-line ORBGRAND order, Sec. III-B:
+ * increasing cost = sum of reliability ranks + c * Hamming weight, the
+ * patterns of one cost and weight being the partitions of that rank sum into
+ * distinct parts <= n):
+ *   0  read from the code's precomputed order table (one 16-byte entry per
+ *      query, copied ahead into shared memory; the default, and the faster);
+ *   1  enumerated by the lanes themselves: lane j of a chunk of 32 queries
+ *      finds the (cost, weight) group of its query from the order's group
+ *      list and unranks its partition with a table of subset counts.
+ * Both give the same query order, hence identical results.  Source 1 applies
+ * to sogrand_decode and to the batched form of square product codes
+ * (product_decode_persistent, product_decode_mixed, product_decode_host, the
+ * server) when thr = 0; every other case reads the table, and the
+ * remaining-mass computation reads it either way.  Source 1 runs kernels of
+ * their own, so the table path's kernels are unaffected by it.
+ *   source   -1 (query only), 0 or 1
+ *   current  HOST out (may be NULL): the source in force
+ * Not to be changed while a decode of this code is in flight.  Errors: EINVAL.
+ */
+int sogrand_code_order_source(sogrand_code *code, int source, int *current);
+
+/*
  * Autotuner: decodes a sample of frames (device [n_frames][n][n] LLRs, with
  * the decode parameters of the intended workload) with the batched form
  * under each schedule (8 or 12 blocks per SM, each with the remaining-mass

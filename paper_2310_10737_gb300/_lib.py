@@ -78,6 +78,7 @@ def load() -> C.CDLL:
         L.sogrand_server_destroy.argtypes = [vp]
         L.sogrand_code_schedule.argtypes = [vp, i32, C.POINTER(C.c_int)]
         L.sogrand_code_dp_area.argtypes = [vp, i32, C.POINTER(C.c_int)]
+        L.sogrand_code_order_source.argtypes = [vp, i32, C.POINTER(C.c_int)]
         L.sogrand_code_tune.argtypes = [vp, i64, vp, i32, i64, f32, f32, i32, C.POINTER(C.c_int),
                                         C.POINTER(C.c_float), vp]
         L.product_decode_mixed.argtypes = [i32, C.POINTER(FrameGroup), i32, i64, f32, f32, i32,
@@ -90,7 +91,7 @@ def load() -> C.CDLL:
                      "sogrand_decode_forney",
                      "product_decode", "product_decode_ex", "product_decode_host", "product_decode_persistent",
                      "sogrand_trace_patterns", "sogrand_release_cached", "sogrand_int_peak",
-                     "product_decode_mixed", "sogrand_code_schedule", "sogrand_code_dp_area", "sogrand_code_tune", "sogrand_server_create",
+                     "product_decode_mixed", "sogrand_code_schedule", "sogrand_code_dp_area", "sogrand_code_order_source", "sogrand_code_tune", "sogrand_server_create",
                      "gldpc_decode",
                      "sogrand_server_submit", "sogrand_server_wait", "sogrand_server_stats", "sogrand_server_destroy"):
             getattr(L, name).restype = C.c_int
@@ -162,6 +163,12 @@ class Code:
         """Set (0 shared, 1 global) or query (-1) where the batched forms keep the remaining-mass area."""
         cur = C.c_int(0)
         _check(load().sogrand_code_dp_area(self.handle, int(where), C.byref(cur)), "sogrand_code_dp_area")
+        return cur.value
+
+    def order_source(self, source: int = -1) -> int:
+        """Set (0 order table, 1 lanes enumerate the order) or query (-1) where the query loop takes its patterns."""
+        cur = C.c_int(0)
+        _check(load().sogrand_code_order_source(self.handle, int(source), C.byref(cur)), "sogrand_code_order_source")
         return cur.value
 
     def tune(self, llr_sample, L: int = 4, query_cap: int = 10**4, thr: float = 0.0, alpha: float = 0.5,

@@ -24,9 +24,11 @@ struct sogrand_code {
   uint64_t *d_hrow = nullptr;  // [m][nm]
   void *d_tab = nullptr;
   sg::DevOrder ord{};
+  sg::DevGroups grp{};
   int jmax = 1;
   int minb = 12;  // schedule: resident blocks per SM (8 or 12), see sogrand_code_tune
   int dp_global = 1;  // schedule: the batched forms keep the remaining-mass area in global memory
+  int ord_lanes = 0;  // 1: lanes enumerate the query order instead of reading the order table
   int64_t tab_cap = 0;
   int64_t tab_bytes = 0;
   std::mutex mu;
@@ -67,6 +69,12 @@ struct HostTables {
   std::vector<uint16_t> cost;   // cost of each entry
   std::vector<int32_t> base, count;
   int ncls = 1, class_size = 0, jmax = 1;
+  // groups (one cost, one weight) of every order and the subset counts that
+  // unrank a pattern within its group (on-lane enumeration)
+  std::vector<uint2> grp;       // x: first entry within the order; y: m | w << 16
+  std::vector<int32_t> gbase;   // first group of order (c, class); one extra end entry
+  std::vector<int32_t> scnt;    // [N = 0..n][w < sc_w][m < sc_m]
+  int sc_w = 1, sc_m = 1;
 };
 
 // cnt[w][m] = number of w-subsets of {1..n} with sum m (saturating), w <= wlim
@@ -163,10 +171,11 @@ int build_tables(int n, int64_t cap, int c_max, bool even, HostTables &T) {
   T.class_size = nb >= 31 ? INT32_MAX : (1 << nb);
   T.base.assign((size_t)(c_max + 1) * ncls, 0);
   T.count.assign((size_t)(c_max + 1) * ncls, 0);
-  int maxcost = 0;
+  int maxcost = 0, maxm = 0;
   for (int c = 0; c <= c_max; c++) {
     for (int K = 0; K < ncls; K++) {
       const size_t start = T.ent.size();
+      T.gbase.push_back((int32_t)T.grp.size());
       const int64_t Ctop = (int64_t)c * n + (int64_t)n * (n + 1) / 2;
       for (int64_t C = 0; C <= Ctop && (int64_t)(T.ent.size() - start) < cap; C++) {
         for (int w = 0; w < wtop; w++) {
@@ -179,6 +188,8 @@ int build_tables(int n, int64_t cap, int c_max, bool even, HostTables &T) {
           const int64_t a = loff[w][li], b = loff[w][li + 1];
           if (b == a) continue;
           if (C > 65535) return SOGRAND_EUNSUPPORTED;
+          T.grp.push_back(make_uint2((unsigned)(T.ent.size() - start), (unsigned)m | ((unsigned)w << 16)));
+          maxm = std::max(maxm, (int)m);
           T.ent.insert(T.ent.end(), stream[w].begin() + a, stream[w].begin() + b);
           T.cost.insert(T.cost.end(), (size_t)(b - a), (uint16_t)C);
           maxcost = std::max(maxcost, (int)C);
@@ -190,6 +201,25 @@ int build_tables(int n, int64_t cap, int c_max, bool even, HostTables &T) {
     }
   }
   T.jmax = maxcost + 2;
+  T.gbase.push_back((int32_t)T.grp.size());
+  // scnt[N][w][m]: w-subsets of {1..N} with sum m (N = 0..n, w < sc_w, m <= the
+  // largest group sum), saturated at INT32_MAX: unranking only subtracts a
+  // count smaller than the index it reduces, which is below the group's size
+  T.sc_w = wtop;
+  T.sc_m = maxm + 1;
+  const size_t plane = (size_t)T.sc_w * T.sc_m;
+  T.scnt.assign((size_t)(n + 1) * plane, 0);
+  T.scnt[0] = 1;
+  for (int N = 1; N <= n; N++) {
+    const int32_t *prev = &T.scnt[(size_t)(N - 1) * plane];
+    int32_t *cur = &T.scnt[(size_t)N * plane];
+    for (int w = 0; w < T.sc_w; w++)
+      for (int m = 0; m < T.sc_m; m++) {
+        int64_t v = prev[(size_t)w * T.sc_m + m];
+        if (w >= 1 && m >= N) v += prev[(size_t)(w - 1) * T.sc_m + (m - N)];
+        cur[(size_t)w * T.sc_m + m] = (int32_t)std::min<int64_t>(v, INT32_MAX);
+      }
+  }
   return SOGRAND_OK;
 }
 
@@ -197,7 +227,9 @@ int upload_tables(sogrand_code *c, const HostTables &T, int64_t cap) {
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t be = T.ent.size() * sizeof(uint4), bc = T.cost.size() * sizeof(uint16_t);
   const size_t bi = T.base.size() * sizeof(int32_t);
-  const size_t bytes = al(be) + al(bc) + 2 * al(bi);
+  const size_t bg = T.grp.size() * sizeof(uint2), bgb = T.gbase.size() * sizeof(int32_t);
+  const size_t bs = T.scnt.size() * sizeof(int32_t);
+  const size_t bytes = al(be) + al(bc) + 2 * al(bi) + al(bg) + al(bgb) + al(bs);
   void *mem = nullptr;
   if (cudaMalloc(&mem, bytes) != cudaSuccess) return SOGRAND_ENOMEM;
   char *p = (char *)mem;
@@ -205,7 +237,13 @@ int upload_tables(sogrand_code *c, const HostTables &T, int64_t cap) {
   uint16_t *dcost = (uint16_t *)(p + al(be));
   int32_t *dbase = (int32_t *)(p + al(be) + al(bc));
   int32_t *dcount = (int32_t *)(p + al(be) + al(bc) + al(bi));
-  if (cudaMemcpy(dent, T.ent.data(), be, cudaMemcpyHostToDevice) != cudaSuccess ||
+  uint2 *dgrp = (uint2 *)(p + al(be) + al(bc) + 2 * al(bi));
+  int32_t *dgbase = (int32_t *)((char *)dgrp + al(bg));
+  int32_t *dscnt = (int32_t *)((char *)dgbase + al(bgb));
+  if (cudaMemcpy(dgrp, T.grp.data(), bg, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dgbase, T.gbase.data(), bgb, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dscnt, T.scnt.data(), bs, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemcpy(dent, T.ent.data(), be, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(dcost, T.cost.data(), bc, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(dbase, T.base.data(), bi, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemcpy(dcount, T.count.data(), bi, cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -223,6 +261,11 @@ int upload_tables(sogrand_code *c, const HostTables &T, int64_t cap) {
   c->ord.count = dcount;
   c->ord.ncls = T.ncls;
   c->ord.class_size = T.class_size;
+  c->grp.grp = dgrp;
+  c->grp.gbase = dgbase;
+  c->grp.scnt = dscnt;
+  c->grp.sc_w = T.sc_w;
+  c->grp.sc_m = T.sc_m;
   c->jmax = T.jmax;
   c->tab_cap = cap;
   c->tab_bytes = (int64_t)bytes;
@@ -256,6 +299,8 @@ sg::DevCode dev_code(const sogrand_code *c) {
   d.jmax = c->jmax;
   d.minb = c->minb;
   d.dp_global = c->dp_global;
+  d.ord_lanes = c->ord_lanes;
+  d.grp = c->grp;
   return d;
 }
 
@@ -873,6 +918,13 @@ int sogrand_code_dp_area(sogrand_code *c, int where, int *current) {
   if (!c || where < -1 || where > 1) return SOGRAND_EINVAL;
   if (where >= 0) c->dp_global = where;
   if (current) *current = c->dp_global;
+  return SOGRAND_OK;
+}
+
+int sogrand_code_order_source(sogrand_code *c, int source, int *current) {
+  if (!c || source < -1 || source > 1) return SOGRAND_EINVAL;
+  if (source >= 0) c->ord_lanes = source;
+  if (current) *current = c->ord_lanes;
   return SOGRAND_OK;
 }
 

@@ -63,7 +63,10 @@ __device__ __forceinline__ void init_block_lock(unsigned char *tl, const SisoPar
 }
 
 // ---------------------------------------------------------------------------
-template <int NPL, class SYN, int MINB>
+// LANES: the query order is enumerated by the lanes (DevCode::ord_lanes)
+// instead of read from the order table; a kernel of its own, so that the
+// table path's code and register allocation stay as they are.
+template <int NPL, class SYN, int MINB, bool LANES>
 __global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const SisoParams P, const DecodeArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   using LY = Layout<NPL, SYN>;
@@ -91,7 +94,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_decode(const DevCode code, const 
     float lapp[NPL];
     WordResult res;
     int used_xf = 0;
-    siso_word<NPL, SYN>(code, P, sc, lam, lane, lapp, res, &used_xf);
+    siso_word<NPL, SYN, LANES>(code, P, sc, lam, lane, lapp, res, &used_xf);
     const bool empty = res.nhit == 0;
 #pragma unroll
     for (int k = 0; k < NPL; k++) {
@@ -192,7 +195,7 @@ static_assert(sizeof(WordCtx) <= 32, "the word's lambda follows the context in t
 // and the second set of words may be wrapped diagonals (a.diag); otherwise
 // it is a square code.n x code.n frame with columns as the second set.
 // Returns the word's query count (-1: non-finite input).
-template <int NPL, class SYN, bool COHERENT, bool GEN>
+template <int NPL, class SYN, bool COHERENT, bool GEN, bool LANES = false>
 __device__ __forceinline__ int product_word(const DevCode &code, const SisoParams &P, const ProductArgs &a,
                                             const Scratch<NPL, SYN> &sc, int64_t f, int wd, int half, int lane) {
   constexpr int NM = (32 * NPL + 63) / 64;
@@ -225,7 +228,7 @@ __device__ __forceinline__ int product_word(const DevCode &code, const SisoParam
     ctx->half = half;
   }
   __syncwarp();
-  siso_word<NPL, SYN>(code, P, sc, lam, lane, lapp, res, &used_xf);
+  siso_word<NPL, SYN, LANES>(code, P, sc, lam, lane, lapp, res, &used_xf);
   bool rows2;
   {
     const volatile WordCtx *vc = ctx;
@@ -580,7 +583,7 @@ __device__ __forceinline__ void frame_after_half(const DevCode &wc, const DevCod
 // square product code whose words all use rowc, with no per-word selection
 // of a code (selecting one of two parameter structs at run time makes the
 // compiler copy it to local memory).
-template <int NPL, class SYN, int MINB, bool GEN>
+template <int NPL, class SYN, int MINB, bool GEN, bool LANES = false>
 __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode rowc, const DevCode colc,
                                                                const SisoParams P, const ProductArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -636,7 +639,7 @@ __global__ void __launch_bounds__(TPB, MINB) k_product_persistent(const DevCode 
     if (lane == 0) half = __ldcg(a.half_cur + f);
     half = __shfl_sync(FULL, half, 0);
     if (lane == 0) reinterpret_cast<WordCtx *>(sc.W())->li = li;
-    const int q = product_word<NPL, SYN, true, GEN>(code, P, a, sc, f, w, half, lane);
+    const int q = product_word<NPL, SYN, true, GEN, LANES>(code, P, a, sc, f, w, half, lane);
     {
       const volatile WordCtx *vc = reinterpret_cast<const volatile WordCtx *>(sc.W());
       f = vc->f;
@@ -736,7 +739,9 @@ template <int NPL, class SYN>
 cudaError_t launch_decode(const DevCode &code, const SisoParams &P, const DecodeArgs &a, cudaStream_t s) {
   if (a.n_words <= 0) return cudaSuccess;
   const int smem = block_scratch_bytes<NPL, SYN>(code.jmax);
-  auto kern = launch_minb(code.minb, a.n_words) == 8 ? k_decode<NPL, SYN, 8> : k_decode<NPL, SYN, 12>;
+  const bool eight = launch_minb(code.minb, a.n_words) == 8, lanes = code.ord_lanes && P.thr <= 0.f;
+  auto kern = lanes ? (eight ? k_decode<NPL, SYN, 8, true> : k_decode<NPL, SYN, 12, true>)
+                    : (eight ? k_decode<NPL, SYN, 8, false> : k_decode<NPL, SYN, 12, false>);
   cudaError_t e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   const int grid = grid_for(kern, smem, a.n_words);
@@ -807,8 +812,10 @@ cudaError_t launch_product_persistent(const DevCode &rowc, const DevCode &colc, 
   const int smem = a.dp_area ? WARPS_PER_BLOCK * Layout<NPL, SYN>::warp_bytes + TAIL_BYTES
                              : block_scratch_bytes<NPL, SYN>(std::max(rowc.jmax, colc.jmax));
   const int64_t words = a.n_frames * std::max(a.nr, a.nc);  // the most words of one half
-  auto kern = launch_minb(rowc.minb, words) == 8 ? k_product_persistent<NPL, SYN, 8, GEN>
-                                                 : k_product_persistent<NPL, SYN, 12, GEN>;
+  // the lanes-enumerated order: the square geometry only (GEN reads the table)
+  const bool eight = launch_minb(rowc.minb, words) == 8, lanes = !GEN && rowc.ord_lanes && P.thr <= 0.f;
+  auto kern = lanes ? (eight ? k_product_persistent<NPL, SYN, 8, GEN, !GEN> : k_product_persistent<NPL, SYN, 12, GEN, !GEN>)
+                    : (eight ? k_product_persistent<NPL, SYN, 8, GEN> : k_product_persistent<NPL, SYN, 12, GEN>);
   e = set_smem(kern, smem);
   if (e != cudaSuccess) return e;
   int occ = 0;

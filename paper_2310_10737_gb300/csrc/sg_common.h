@@ -32,6 +32,19 @@ struct DevOrder {
   int32_t class_size;     // patterns in one class (saturated): count == class_size means the whole class
 };
 
+// The same orders as groups, for lanes that enumerate their patterns instead
+// of reading DevOrder::ent (DevCode::ord_lanes): a group is the run of
+// patterns of one cost and one Hamming weight w, i.e. the w-subsets of the
+// ranks {1..n} with rank sum m = cost - c w, in lexicographic order.  (A
+// struct apart from DevOrder, which the kernels copy to local memory when
+// they pass it to out-of-line functions.)
+struct DevGroups {
+  const uint2 *grp;       // [groups] x: first entry of the group within its order; y: m | w << 16
+  const int32_t *gbase;   // [(c_max+1) * ncls + 1] first group of order (c, class)
+  const int32_t *scnt;    // [(n+1) * sc_w * sc_m] w-subsets of {1..N} with sum m at (N, w, m), saturated
+  int32_t sc_w, sc_m;     // extents of scnt in w and m
+};
+
 struct DevCode {
   int32_t n, k, m;       // length, dimension, parity checks (m = n - k)
   int32_t even;          // 1: even code, search restricted to the parity of y
@@ -43,6 +56,8 @@ struct DevCode {
   int32_t jmax;          // largest stored cost + 2 (bounds the remaining-mass DP)
   int32_t minb;          // schedule: resident blocks per SM the kernels are compiled for (8 or 12)
   int32_t dp_global;     // schedule: the batched forms keep the remaining-mass area in global memory
+  int32_t ord_lanes;     // 1: the lanes enumerate the query order (loop without the threshold rule)
+  DevGroups grp;         // the order's groups (used with ord_lanes)
 };
 
 struct SisoParams {

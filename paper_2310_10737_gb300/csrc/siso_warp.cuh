@@ -1139,6 +1139,140 @@ __device__ __noinline__ LoopOut query_loop_plain(const Scratch<NPL, SYN> sc, con
   return LoopOut{q, nhit, wacc, tmass};
 }
 
+// ----------------------------------------------------------------------------
+// the query order enumerated by the lanes (instead of read from the table)
+// ----------------------------------------------------------------------------
+// 1-line ORBGRAND (Sec. III-B) queries the patterns in order of cost = sum of
+// ranks + c * weight; the patterns of one cost and weight w are the
+// partitions of m = cost - c w into w distinct parts <= n (rank sets), taken
+// in lexicographic order of the ascending rank vector.  Pattern o of such a
+// group is found part by part: with the parts so far summing to m - m', wl
+// parts left and each part above the last one (at least a0), part a is taken
+// if o is below the number of ways to finish after it, and otherwise o drops
+// by that number and a grows.  The ways to finish after a are the
+// (wl - 1)-subsets of {a+1..n} with sum m' - a, i.e. (subtracting a from
+// each) the (wl - 1)-subsets of {1..n-a} with sum m' - wl a, read from the
+// table of subset counts.  The last two parts follow in closed form: the
+// pairs {a, m' - a} in order of a, from max(a0, m' - n).  The pattern is
+// written as a table entry (weight byte, 0-based rank bytes, n in the unused
+// bytes) into the lane's 16-byte slot and read back.
+__device__ __forceinline__ uint4 unrank_entry(const int32_t *scnt, int sc_w, int sc_m, int n, int w, int m, int o,
+                                              uint4 *slot) {
+  unsigned char *b = reinterpret_cast<unsigned char *>(slot);
+  const unsigned nn = (unsigned)n * 0x01010101u;
+  *slot = make_uint4((nn & ~0xffu) | (unsigned)w, nn, nn, nn);
+  int lo = 1;
+#pragma unroll 1
+  for (int i = 0; i < w - 2; i++) {
+    const int wl = w - i;
+    int a = lo;
+#pragma unroll 1
+    for (; a < n; a++) {  // bounded: for an index inside the group the count is reached by a = n - 1
+      const int mm = m - wl * a;
+      const int cnt = mm < 0 ? 0 : __ldg(scnt + ((n - a) * sc_w + (wl - 1)) * sc_m + mm);
+      if (o < cnt) break;
+      o -= cnt;
+    }
+    b[1 + i] = (unsigned char)(a - 1);
+    m -= a;
+    lo = a + 1;
+  }
+  // (the clamps keep every rank byte a valid record index, n the neutral one,
+  // whatever the arguments; for an offset inside its group they change nothing)
+  if (w >= 2) {
+    const int a = max(lo, m - n) + o;
+    b[w - 1] = (unsigned char)min(max(a - 1, 0), n);
+    b[w] = (unsigned char)min(max(m - a - 1, 0), n);
+  } else if (w == 1) {
+    b[1] = (unsigned char)min(max(m - 1, 0), n);
+  }
+  return *slot;
+}
+
+// The thr = 0 query loop with the order enumerated by the lanes: the same
+// chunks of 32 queries, syndromes, masses and hit recording as
+// query_loop_plain; lane j finds the group of query q0 + j from the group
+// starts of the chunk (one coalesced load of the next 32 group records, a
+// bit mask of the groups that start inside the chunk) and unranks its offset
+// in that group.  The order's groups are grp[g0 .. ge - 1]; the arguments are
+// plain values and pointers (a reference to the kernel's code parameter would
+// make the compiler copy the parameter to local memory).
+template <int NPL, class SYN>
+__device__ __noinline__ LoopOut query_loop_lanes(const Scratch<NPL, SYN> sc, const WordHead<NPL, SYN> &h,
+                                                 const uint2 *grp, int g0, int ge, const int32_t *scnt, int sc_w,
+                                                 int sc_m, int n, int qlim, int L, int lane) {
+  int q = 0, nhit = 0, wacc = 0;
+  DF tmass = {0.f, 0.f};
+  int g = g0;  // the group holding query q (warp-uniform)
+  unsigned gx = 0, gy = g < ge ? __ldg(&grp[g].y) : 0u;  // its start and m | w << 16
+  uint4 *slot = sc.pf() + lane;
+  for (;;) {
+    const int lim = min(32, qlim - q);
+    if (lim <= 0) break;
+    // the next 32 group records; d = start - q >= 1 (group g holds q)
+    const int gi = g + 1 + lane;
+    const uint2 r = gi < ge ? __ldg(grp + gi) : make_uint2(0x7fffffffu, 0u);
+    const int d = (int)r.x - q;
+    const unsigned starts = __reduce_or_sync(FULL, d < 32 ? 1u << d : 0u);  // groups starting in the chunk
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int rg = __popc(starts & upto);  // groups started after q and at or before q + lane
+    const unsigned sx = __shfl_sync(FULL, r.x, rg > 0 ? rg - 1 : 0);
+    const unsigned sy = __shfl_sync(FULL, r.y, rg > 0 ? rg - 1 : 0);
+    const unsigned my = rg > 0 ? sy : gy;
+    const int mo = q + lane - (int)(rg > 0 ? sx : gx);
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < lim) e = unrank_entry(scnt, sc_w, sc_m, n, (int)(my >> 16), (int)(my & 0xffffu), mo, slot);
+    // the group holding q + 32: every group that starts at or before it
+    const int adv = __popc(__ballot_sync(FULL, d <= 32));
+    if (adv > 0) {
+      gx = __shfl_sync(FULL, r.x, adv - 1);
+      gy = __shfl_sync(FULL, r.y, adv - 1);
+      g += adv;
+    }
+    const int w = e.x & 0xff;
+    const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
+    DF mass;
+    const SYN s = ent_syndrome<SYN>(e, w, wmax, sc.hr(), mass) ^ h.s0;
+    const bool hit = lane < lim && s == 0;
+    unsigned hm = __ballot_sync(FULL, hit);
+    int stop_lane = -1;
+    while (hm) {
+      const int hl = __ffs(hm) - 1;
+      hm &= hm - 1;
+      record_hit<NPL, SYN>(sc, h, e, hl, nhit, lane);
+      nhit++;
+      if (nhit >= L) {
+        stop_lane = hl;
+        break;
+      }
+    }
+    if (stop_lane >= 0) {
+      if (lane <= stop_lane) {
+        wacc += w;
+        df_acc(tmass, mass);
+      }
+      q += stop_lane + 1;
+      break;
+    }
+    wacc += w;
+    df_acc(tmass, mass);
+    q += lim;
+  }
+  return LoopOut{q, nhit, wacc, tmass};
+}
+
+// The thr = 0 query loop of a word: patterns from the order table, or
+// enumerated by the lanes (LANES, kernels of their own).
+template <int NPL, class SYN, bool LANES>
+__device__ __forceinline__ LoopOut query_loop(const Scratch<NPL, SYN> &sc, const WordHead<NPL, SYN> &h,
+                                              const DevCode &code, int ti, int tb, int qlim, int L, int lane) {
+  if constexpr (LANES)
+    return query_loop_lanes<NPL, SYN>(sc, h, code.grp.grp, __ldg(code.grp.gbase + ti), __ldg(code.grp.gbase + ti + 1),
+                                      code.grp.scnt, code.grp.sc_w, code.grp.sc_m, code.n, qlim, L, lane);
+  else
+    return query_loop_plain<NPL, SYN>(sc, h, code.ord.ent + tb, qlim, L, lane);
+}
+
 // lam[k] is bit lane + 32k of the SISO input lambda = fl32(L_Ch + L_A)
 // (the caller loads it; entries past n are ignored).  On return lapp[k] holds
 // L_APP for the same bits, res the per-word results; the list (in query
@@ -1146,7 +1280,7 @@ __device__ __noinline__ LoopOut query_loop_plain(const Scratch<NPL, SYN> sc, con
 // sc.lp() (log p(z)/p(0)) and sc.wl() (APP of each word).  *flags (if given)
 // collects the remaining-mass flags (bit 0: extended range; bit 1: the
 // block's remaining-mass area could not be locked).
-template <int NPL, class SYN>
+template <int NPL, class SYN, bool LANES = false>
 __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratch<NPL, SYN> &sc,
                           const float (&lam)[NPL], int lane, float (&lapp)[NPL], WordResult &res,
                           int *flags = nullptr) {
@@ -1195,7 +1329,7 @@ __device__ void siso_word(const DevCode &code, const SisoParams &P, const Scratc
   // warp's shared area while the current chunk is tested (cp.async: no
   // registers held, the L2 latency overlaps the chunk's work)
   if (P.thr <= 0.f) {  // no threshold rule: the out-of-line loop
-    const LoopOut lo = query_loop_plain<NPL, SYN>(sc, h, O.ent + tb, qlim, P.L, lane);
+    const LoopOut lo = query_loop<NPL, SYN, LANES>(sc, h, code, ti, tb, qlim, P.L, lane);
     q = lo.q;
     nhit = lo.nhit;
     wacc = lo.wacc;

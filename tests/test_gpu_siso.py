@@ -98,6 +98,38 @@ def test_siso_ties_and_zeros(env, oracle_lib, name):
     compare_siso(lc, out, ref, "ties")
 
 
+@pytest.mark.parametrize("name", ["ebch_32_26", "ebch_64_57", "ebch_128_120"])
+def test_siso_near_ties_in_the_last_mantissa_bits(env, oracle_lib, name):
+    """Reliabilities that differ only in their last few mantissa bits, mostly
+    with the larger one at the lower bit index (the rank order of Sec. III-B,
+    ties by index, must follow the exact values): the kernel sorts on keys
+    that keep |lambda| without its low mantissa bits, so these words take its
+    exact second sort.  The pairs sit among the least reliable bits, whose
+    ranks the first queries use, so a wrong order changes queries and lists."""
+    lc = ebch(name)
+    W, n = 600, lc.n
+    _, _, lch = awgn_words(lc, W, 3.0, seed=83)
+    mag = np.abs(lch).astype(np.float32)
+    bits = mag.view(np.uint32) & np.uint32(0xFFFFFF00)  # low 8 mantissa bits cleared
+    rng = np.random.default_rng(9)
+    for w in range(W):
+        low = np.argsort(mag[w], kind="stable")[: n // 2]
+        pairs = rng.permutation(low)[: 2 * (len(low) // 4)].reshape(-1, 2)
+        for i, j in pairs:
+            i, j = min(i, j), max(i, j)
+            bits[w, j] = bits[w, i]
+            d = np.uint32(rng.integers(1, 32))  # stays below every key's dropped bits
+            u = rng.random()
+            if u < 0.7:
+                bits[w, i] += d  # larger value at the lower index: against the index order
+            elif u < 0.9:
+                bits[w, j] += d  # with the index order
+            # else: an exact tie, broken by the index
+    lch2 = np.where(lch < 0, -1.0, 1.0).astype(np.float32) * bits.view(np.float32)
+    lc, out, ref = _run(env, oracle_lib, name, lch2, L=4, what=f"{name} near ties")
+    compare_siso(lc, out, ref, f"{name} near ties")
+
+
 def test_siso_small_caps_empty_lists_and_list16(env, oracle_lib):
     lc = ebch("ebch_32_26")
     _, _, lch = awgn_words(lc, 700, 1.5, seed=80)
