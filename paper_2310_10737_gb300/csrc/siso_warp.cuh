@@ -321,48 +321,49 @@ __device__ __forceinline__ void dp_unlock(int *lock, bool held, int lane) {
 // ----------------------------------------------------------------------------
 // warp helpers
 // ----------------------------------------------------------------------------
-// Bitonic sort of the warp's 32 * NPL keys, ascending (lane l holds keys
-// l, l + 32, ...).  The stages run as loops rather than unrolled: the sort is
-// straight-line work done once per word, and its unrolled form (about 20
-// stages of shuffles) made the kernel's code large enough that warps in other
-// phases of their words stalled on instruction fetch (measured 4-10% slower
-// for codes of 64 and 128 bits).
-// Compare-exchange of keys k and k ^ kj held by the same lane (stage distance
-// 32 kj); kj is one of the powers of two below NPL.
+// Bitonic sort of the warp's 32 * NPL keys, ascending, lane l holding sorted
+// positions l NPL .. l NPL + NPL - 1 (blocked).  The exchanges at distance
+// j < NPL stay inside a lane's registers, so fewer stages need shuffles (15
+// of 21 for 64 keys, 15 of 28 for 128; 20 and 25 when lane l held positions
+// l, l + 32, ...: 1-3% faster per word, most for 128-bit codes).  The stages
+// run as loops rather than unrolled: the sort is straight-line work done once
+// per word, and its unrolled form (about 20 stages of shuffles) made the
+// kernel's code large enough that warps in other phases of their words
+// stalled on instruction fetch (measured 4-10% slower for codes of 64 and 128
+// bits).
 template <int NPL>
-__device__ __forceinline__ void cmpx_regs(uint64_t (&v)[NPL], int kj, int size, int lane) {
-#pragma unroll
-  for (int k = 0; k < NPL; k++) {
-#pragma unroll
-    for (int c = 1; c < NPL; c <<= 1) {
-      if (c == kj && (k ^ c) > k) {
-        const int kp = k ^ c;
-        const bool asc = ((k * 32 + lane) & size) == 0;
-        uint64_t a = v[k], b = v[kp];
-        bool sw = asc ? (a > b) : (a < b);
-        v[k] = sw ? b : a;
-        v[kp] = sw ? a : b;
-      }
-    }
-  }
-}
-template <int NPL>
-__device__ __forceinline__ void warp_bitonic_sort(uint64_t (&v)[NPL], int lane) {
+__device__ __forceinline__ void warp_bitonic_sort_blocked(uint64_t (&v)[NPL], int lane) {
   constexpr int N = 32 * NPL;
 #pragma unroll 1
   for (int size = 2; size <= N; size <<= 1) {
-    if (NPL > 1) {
 #pragma unroll 1
-      for (int j = size >> 1; j >= 32; j >>= 1) cmpx_regs<NPL>(v, j >> 5, size, lane);
-    }
-#pragma unroll 1
-    for (int j = min(size >> 1, 16); j > 0; j >>= 1) {
+    for (int j = size >> 1; j >= NPL; j >>= 1) {
+      const int lj = j / NPL;  // partner lane: lane ^ lj, same register
 #pragma unroll
       for (int k = 0; k < NPL; k++) {
-        uint64_t o = __shfl_xor_sync(FULL, v[k], j);
-        const bool asc = ((k * 32 + lane) & size) == 0;
-        const bool lower = (lane & j) == 0;
+        const uint64_t o = __shfl_xor_sync(FULL, v[k], lj);
+        const int p = lane * NPL + k;
+        const bool asc = (p & size) == 0;
+        const bool lower = (lane & lj) == 0;
         v[k] = (lower == asc) ? (v[k] < o ? v[k] : o) : (v[k] < o ? o : v[k]);
+      }
+    }
+    if constexpr (NPL > 1) {
+#pragma unroll
+      for (int j = NPL / 2; j > 0; j >>= 1) {
+        if (j <= (size >> 1)) {
+#pragma unroll
+          for (int k = 0; k < NPL; k++) {
+            if ((k & j) == 0) {
+              const int kp = k | j;
+              const bool asc = ((lane * NPL + k) & size) == 0;
+              const uint64_t a = v[k], b = v[kp];
+              const bool sw = asc ? (a > b) : (a < b);
+              v[k] = sw ? b : a;
+              v[kp] = sw ? a : b;
+            }
+          }
+        }
       }
     }
   }
@@ -937,11 +938,11 @@ __device__ bool siso_prologue(const DevCode &code, const Scratch<NPL, SYN> &sc, 
     const int i = lane + 32 * k;
     key[k] = i < n ? (((uint64_t)__float_as_uint(fabsf(lam[k])) << 32) | (uint64_t)i) : ~0ull;
   }
-  warp_bitonic_sort<NPL>(key, lane);
+  warp_bitonic_sort_blocked<NPL>(key, lane);
   int64_t sy = 0, sxy = 0;
 #pragma unroll
   for (int k = 0; k < NPL; k++) {
-    const int e = k * 32 + lane;
+    const int e = lane * NPL + k;  // sorted position (blocked layout)
     if (e < n) {
       const float a = __uint_as_float((unsigned)(key[k] >> 32));
       const int idx = (int)(key[k] & 0xffffffffu);
