@@ -507,7 +507,7 @@ def main():
                     help="persistent: one kernel per decode with a device-side frame queue; plain: one launch per half")
     ap.add_argument("--plain-steps", type=int, default=3, help="steps of the other form, timed for comparison (0: off)")
     ap.add_argument("--serve-requests", type=int, default=1200, help="requests per offered load in the serving run (0: off)")
-    ap.add_argument("--serve-loads", default="250,500,1000,2000", help="offered loads, requests/s")
+    ap.add_argument("--serve-loads", default="250,500,1000,2000,3000", help="offered loads, requests/s")
     ap.add_argument("--other-configs", type=int, default=1, help="1: also measure the C1, C2 and C4 workloads")
     args = ap.parse_args()
     if args.impl == "reference":
