@@ -44,11 +44,11 @@ METRIC = "decoded info bits/s, eBCH(64,57)^2 product code"
 # capture of a 10,000-frame decode of this workload (traffic grows with the
 # frame count at a fixed Eb/N0 mix), valid only for the kernel sources whose
 # digest is recorded with it: `traffic` is null once they change.
-TRAFFIC = {"csrc_digest": "958c354a724274b8e0d896dff97da0d5efecf90b0fa4f85d3f9922a275d91eaa",
-           "bytes_per_frame": 279158.0,
+TRAFFIC = {"csrc_digest": "f6a931810f509a673668d4db930d62b4cc9f7661ce62958ec9f7ce4da77631f4",
+           "bytes_per_frame": 280960.5,
            "source": "profiles/k_product_persistent_ebch64_57sq_10k_frames.md",
            # pipe activity of the same capture (percent of peak sustained over active cycles)
-           "ncu": {"issue_active_pct": 68.8, "alu_pipe_pct": 47.4, "fma_pipe_pct": 26.8,
+           "ncu": {"issue_active_pct": 68.8, "alu_pipe_pct": 45.6, "fma_pipe_pct": 25.8,
                    "tensor_pipe_pct": 0.0, "dram_throughput_pct": 1.5}}
 
 

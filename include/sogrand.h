@@ -423,7 +423,9 @@ int product_decode_noalloc(sogrand_code *row_code, const sogrand_code *col_code,
                            uint8_t *bits, int32_t *half_iters, uint8_t *status, int64_t *queries, void *stream);
 
 /*
- * Test hook: the device's canonical query order for one word.
+ * Test hook: the device's canonical query order for one word, from the
+ * order table or, with sogrand_code_order_source(code, 1), as the lanes
+ * enumerate it.
  *   llr          HOST [n] lambda values
  *   max_q        number of queries to list, >= 1
  *   patterns_out HOST [max_q][ceil(n/64)] u64 noise patterns in RANK space:

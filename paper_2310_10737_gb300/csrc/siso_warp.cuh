@@ -984,6 +984,100 @@ __device__ __forceinline__ void ent_mask(const uint4 &e, uint64_t (&m)[NM]) {
 #undef SG_M
 }
 
+// ----------------------------------------------------------------------------
+// the query order enumerated by the lanes (instead of read from the table)
+// ----------------------------------------------------------------------------
+// 1-line ORBGRAND (Sec. III-B) queries the patterns in order of cost = sum of
+// ranks + c * weight; the patterns of one cost and weight w are the
+// partitions of m = cost - c w into w distinct parts <= n (rank sets), taken
+// in lexicographic order of the ascending rank vector.  Pattern o of such a
+// group is found part by part: with the parts so far summing to m - m', wl
+// parts left and each part above the last one (at least a0), part a is taken
+// if o is below the number of ways to finish after it, and otherwise o drops
+// by that number and a grows.  The ways to finish after a are the
+// (wl - 1)-subsets of {a+1..n} with sum m' - a, i.e. (subtracting a from
+// each) the (wl - 1)-subsets of {1..n-a} with sum m' - wl a, read from the
+// table of subset counts.  The last two parts follow in closed form: the
+// pairs {a, m' - a} in order of a, from max(a0, m' - n).  The pattern is
+// written as a table entry (weight byte, 0-based rank bytes, n in the unused
+// bytes) into the lane's 16-byte slot and read back.
+__device__ __forceinline__ uint4 unrank_entry(const int32_t *scnt, int sc_w, int sc_m, int n, int w, int m, int o,
+                                              uint4 *slot) {
+  unsigned char *b = reinterpret_cast<unsigned char *>(slot);
+  const unsigned nn = (unsigned)n * 0x01010101u;
+  *slot = make_uint4((nn & ~0xffu) | (unsigned)w, nn, nn, nn);
+  int lo = 1;
+#pragma unroll 1
+  for (int i = 0; i < w - 2; i++) {
+    const int wl = w - i;
+    int a = lo;
+#pragma unroll 1
+    for (; a < n; a++) {  // bounded: for an index inside the group the count is reached by a = n - 1
+      const int mm = m - wl * a;
+      const int cnt = mm < 0 ? 0 : __ldg(scnt + ((n - a) * sc_w + (wl - 1)) * sc_m + mm);
+      if (o < cnt) break;
+      o -= cnt;
+    }
+    b[1 + i] = (unsigned char)(a - 1);
+    m -= a;
+    lo = a + 1;
+  }
+  // (the clamps keep every rank byte a valid record index, n the neutral one,
+  // whatever the arguments; for an offset inside its group they change nothing)
+  if (w >= 2) {
+    const int a = max(lo, m - n) + o;
+    b[w - 1] = (unsigned char)min(max(a - 1, 0), n);
+    b[w] = (unsigned char)min(max(m - a - 1, 0), n);
+  } else if (w == 1) {
+    b[1] = (unsigned char)min(max(m - 1, 0), n);
+  }
+  return *slot;
+}
+
+// The group window of the lane-enumerated order: the group holding query q
+// (warp-uniform: its index g, start gx and record gy) and, for a chunk of 32
+// queries q .. q + 31, each lane's group and its offset there, from one
+// coalesced load of the next 32 group records (group starts after q are at
+// least q + 1, and at most 32 of them fall in q + 1 .. q + 32) and a bit mask
+// of the groups that start inside the chunk.  Order (c, class) owns groups
+// g0 .. ge - 1.
+struct GroupWindow {
+  const uint2 *grp;
+  int g, ge;
+  unsigned gx, gy;
+  __device__ __forceinline__ void init(const uint2 *grp_, int g0, int ge_) {
+    grp = grp_;
+    g = g0;
+    ge = ge_;
+    gx = 0u;
+    gy = g < ge ? __ldg(&grp[g].y) : 0u;
+  }
+  // lane's pattern for query q + lane (an empty entry for lane >= lim), then
+  // the window moves on to the group holding q + 32
+  __device__ __forceinline__ uint4 chunk(int q, int lim, int lane, const int32_t *scnt, int sc_w, int sc_m, int n,
+                                         uint4 *slot) {
+    const int gi = g + 1 + lane;
+    const uint2 r = gi < ge ? __ldg(grp + gi) : make_uint2(0x7fffffffu, 0u);
+    const int d = (int)r.x - q;
+    const unsigned starts = __reduce_or_sync(FULL, d < 32 ? 1u << d : 0u);  // groups starting in the chunk
+    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+    const int rg = __popc(starts & upto);  // groups started after q and at or before q + lane
+    const unsigned sx = __shfl_sync(FULL, r.x, rg > 0 ? rg - 1 : 0);
+    const unsigned sy = __shfl_sync(FULL, r.y, rg > 0 ? rg - 1 : 0);
+    const unsigned my = rg > 0 ? sy : gy;
+    const int mo = q + lane - (int)(rg > 0 ? sx : gx);
+    uint4 e = make_uint4(0u, 0u, 0u, 0u);
+    if (lane < lim) e = unrank_entry(scnt, sc_w, sc_m, n, (int)(my >> 16), (int)(my & 0xffffu), mo, slot);
+    const int adv = __popc(__ballot_sync(FULL, d <= 32));
+    if (adv > 0) {
+      gx = __shfl_sync(FULL, r.x, adv - 1);
+      gy = __shfl_sync(FULL, r.y, adv - 1);
+      g += adv;
+    }
+    return e;
+  }
+};
+
 // The canonical query order for one input (test hook): writes the first
 // max_q rank masks (NM words each); returns how many were written.
 template <int NPL, class SYN>
@@ -996,11 +1090,26 @@ __device__ int trace_word(const DevCode &code, const Scratch<NPL, SYN> &sc, cons
   const int ti = h.c * O.ncls + (code.even ? h.par : 0);
   const int tb = __ldg(O.base + ti), tc = __ldg(O.count + ti);
   const int qn = min(max_q, tc);
-  for (int q = lane; q < qn; q += 32) {
-    uint64_t m[NM];
-    ent_mask<NM>(__ldg(O.ent + tb + q), m);
+  if (code.ord_lanes) {  // the order as the lanes enumerate it
+    GroupWindow W;
+    W.init(code.grp.grp, __ldg(code.grp.gbase + ti), __ldg(code.grp.gbase + ti + 1));
+    for (int q0 = 0; q0 < qn; q0 += 32) {
+      const uint4 e = W.chunk(q0, min(32, qn - q0), lane, code.grp.scnt, code.grp.sc_w, code.grp.sc_m, code.n,
+                              sc.pf() + lane);
+      if (q0 + lane < qn) {
+        uint64_t m[NM];
+        ent_mask<NM>(e, m);
 #pragma unroll
-    for (int x = 0; x < NM; x++) out[(size_t)q * NM + x] = m[x];
+        for (int x = 0; x < NM; x++) out[(size_t)(q0 + lane) * NM + x] = m[x];
+      }
+    }
+  } else {
+    for (int q = lane; q < qn; q += 32) {
+      uint64_t m[NM];
+      ent_mask<NM>(__ldg(O.ent + tb + q), m);
+#pragma unroll
+      for (int x = 0; x < NM; x++) out[(size_t)q * NM + x] = m[x];
+    }
   }
   if (c_out && lane == 0) *c_out = h.c;
   return qn;
@@ -1140,56 +1249,6 @@ __device__ __noinline__ LoopOut query_loop_plain(const Scratch<NPL, SYN> sc, con
   return LoopOut{q, nhit, wacc, tmass};
 }
 
-// ----------------------------------------------------------------------------
-// the query order enumerated by the lanes (instead of read from the table)
-// ----------------------------------------------------------------------------
-// 1-line ORBGRAND (Sec. III-B) queries the patterns in order of cost = sum of
-// ranks + c * weight; the patterns of one cost and weight w are the
-// partitions of m = cost - c w into w distinct parts <= n (rank sets), taken
-// in lexicographic order of the ascending rank vector.  Pattern o of such a
-// group is found part by part: with the parts so far summing to m - m', wl
-// parts left and each part above the last one (at least a0), part a is taken
-// if o is below the number of ways to finish after it, and otherwise o drops
-// by that number and a grows.  The ways to finish after a are the
-// (wl - 1)-subsets of {a+1..n} with sum m' - a, i.e. (subtracting a from
-// each) the (wl - 1)-subsets of {1..n-a} with sum m' - wl a, read from the
-// table of subset counts.  The last two parts follow in closed form: the
-// pairs {a, m' - a} in order of a, from max(a0, m' - n).  The pattern is
-// written as a table entry (weight byte, 0-based rank bytes, n in the unused
-// bytes) into the lane's 16-byte slot and read back.
-__device__ __forceinline__ uint4 unrank_entry(const int32_t *scnt, int sc_w, int sc_m, int n, int w, int m, int o,
-                                              uint4 *slot) {
-  unsigned char *b = reinterpret_cast<unsigned char *>(slot);
-  const unsigned nn = (unsigned)n * 0x01010101u;
-  *slot = make_uint4((nn & ~0xffu) | (unsigned)w, nn, nn, nn);
-  int lo = 1;
-#pragma unroll 1
-  for (int i = 0; i < w - 2; i++) {
-    const int wl = w - i;
-    int a = lo;
-#pragma unroll 1
-    for (; a < n; a++) {  // bounded: for an index inside the group the count is reached by a = n - 1
-      const int mm = m - wl * a;
-      const int cnt = mm < 0 ? 0 : __ldg(scnt + ((n - a) * sc_w + (wl - 1)) * sc_m + mm);
-      if (o < cnt) break;
-      o -= cnt;
-    }
-    b[1 + i] = (unsigned char)(a - 1);
-    m -= a;
-    lo = a + 1;
-  }
-  // (the clamps keep every rank byte a valid record index, n the neutral one,
-  // whatever the arguments; for an offset inside its group they change nothing)
-  if (w >= 2) {
-    const int a = max(lo, m - n) + o;
-    b[w - 1] = (unsigned char)min(max(a - 1, 0), n);
-    b[w] = (unsigned char)min(max(m - a - 1, 0), n);
-  } else if (w == 1) {
-    b[1] = (unsigned char)min(max(m - 1, 0), n);
-  }
-  return *slot;
-}
-
 // The thr = 0 query loop with the order enumerated by the lanes: the same
 // chunks of 32 queries, syndromes, masses and hit recording as
 // query_loop_plain; lane j finds the group of query q0 + j from the group
@@ -1204,32 +1263,13 @@ __device__ __noinline__ LoopOut query_loop_lanes(const Scratch<NPL, SYN> sc, con
                                                  int sc_m, int n, int qlim, int L, int lane) {
   int q = 0, nhit = 0, wacc = 0;
   DF tmass = {0.f, 0.f};
-  int g = g0;  // the group holding query q (warp-uniform)
-  unsigned gx = 0, gy = g < ge ? __ldg(&grp[g].y) : 0u;  // its start and m | w << 16
+  GroupWindow W;
+  W.init(grp, g0, ge);
   uint4 *slot = sc.pf() + lane;
   for (;;) {
     const int lim = min(32, qlim - q);
     if (lim <= 0) break;
-    // the next 32 group records; d = start - q >= 1 (group g holds q)
-    const int gi = g + 1 + lane;
-    const uint2 r = gi < ge ? __ldg(grp + gi) : make_uint2(0x7fffffffu, 0u);
-    const int d = (int)r.x - q;
-    const unsigned starts = __reduce_or_sync(FULL, d < 32 ? 1u << d : 0u);  // groups starting in the chunk
-    const unsigned upto = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
-    const int rg = __popc(starts & upto);  // groups started after q and at or before q + lane
-    const unsigned sx = __shfl_sync(FULL, r.x, rg > 0 ? rg - 1 : 0);
-    const unsigned sy = __shfl_sync(FULL, r.y, rg > 0 ? rg - 1 : 0);
-    const unsigned my = rg > 0 ? sy : gy;
-    const int mo = q + lane - (int)(rg > 0 ? sx : gx);
-    uint4 e = make_uint4(0u, 0u, 0u, 0u);
-    if (lane < lim) e = unrank_entry(scnt, sc_w, sc_m, n, (int)(my >> 16), (int)(my & 0xffffu), mo, slot);
-    // the group holding q + 32: every group that starts at or before it
-    const int adv = __popc(__ballot_sync(FULL, d <= 32));
-    if (adv > 0) {
-      gx = __shfl_sync(FULL, r.x, adv - 1);
-      gy = __shfl_sync(FULL, r.y, adv - 1);
-      g += adv;
-    }
+    const uint4 e = W.chunk(q, lim, lane, scnt, sc_w, sc_m, n, slot);
     const int w = e.x & 0xff;
     const int wmax = (int)__reduce_max_sync(FULL, (unsigned)w);
     DF mass;
