@@ -697,6 +697,12 @@ def main():
         cpu = {"value": rate, "unit": "bits/s", "cores": cores, "kind": "oracle",
                "sample": f"first {args.cpu_frames} frames of the workload ({args.cpu_frames // 7} per Eb/N0 point), "
                          f"{dt:.1f} s wall"}
+        # the same oracle on one host core (a smaller sample of the same frames)
+        n1 = min(args.cpu_frames, 140)
+        rate1, dt1 = cpu_oracle_rate(code, lch[:n1], 1)
+        log(f"cpu baseline, one core: {n1} frames in {dt1:.1f} s")
+        cpu["single_core"] = {"value": rate1, "unit": "bits/s", "cores": 1,
+                              "sample": f"first {n1} frames of the workload, {dt1:.1f} s wall"}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "bits/s", "n_gpus": world, "steps": args.steps,
