@@ -365,9 +365,10 @@ int product_decode_mixed(int n_groups, const sogrand_frame_group *groups, int L,
 /*
  * product_decode on HOST buffers: copies llr_ch to the device, decodes with
  * the batched form (product_decode_persistent) and copies the results back
- * before returning.  Batches of 4096 frames or more are split into up to 8
- * chunks whose host-to-device copy, decoding (two internal streams, chunks in
- * turn) and device-to-host copy overlap; the internal streams start after the
+ * before returning.  The batch is split into chunks of 2048 frames, then
+ * twice as many each time up to a quarter of the batch (7 chunks for 100,000
+ * frames), whose host-to-device copy, decoding (two internal streams, chunks
+ * in turn) and device-to-host copy overlap; the internal streams start after the
  * work already queued on `stream`, and `stream` is synchronised before the
  * call returns.  Device buffers come from the library's memory pool and are
  * freed before return.  Pinned host memory makes the copies asynchronous DMA

@@ -992,19 +992,31 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   // copy in (h2d), decode (two streams taking chunks in turn, so the tail of
   // one chunk overlaps the start of the next), copy out (d2h).  Events order
   // the stages of each chunk; all streams start after the caller's stream.
-  const int64_t K = std::max<int64_t>(1, std::min<int64_t>(8, F / 2048));
-  const int64_t chunk = (F + K - 1) / K;
+  // Chunk sizes: 2048 frames first, doubling up to a quarter of the batch,
+  // so that decoding starts after a short copy and each later copy takes
+  // less time than the decoding of the chunk before it (about every other
+  // call the copy in runs at ~15 GB/s instead of ~210 GB/s on a GB300), with
+  // few chunks, since each adds a launch tail.
+  const int64_t cmax = std::max<int64_t>(2048, (F + 3) / 4);
+  std::vector<int64_t> starts;
+  for (int64_t f0 = 0, ck = std::min<int64_t>(2048, F); f0 < F; f0 += ck, ck = std::min(2 * ck, cmax))
+    starts.push_back(f0);
+  starts.push_back(F);
+  const int64_t K = (int64_t)starts.size() - 1;
+  int64_t chunk = 0;
+  for (int64_t k = 0; k < K; k++) chunk = std::max(chunk, starts[k + 1] - starts[k]);
   const size_t b_in = al256((size_t)F * in_f), b_bits = al256((size_t)F * nb);
   const size_t b_out = b_in + b_bits + al256((size_t)F * 4) + al256((size_t)F) + al256((size_t)F * 8);
   const size_t b_scr = al256(persistent_scratch_bytes(chunk, nr, nc, nm, max_iter)) + dp_region_bytes(c, cc);
   char *mem = nullptr;
-  if (scratch_alloc(&mem, b_out + 2 * b_scr + 256, s) != cudaSuccess) return SOGRAND_ENOMEM;
+  if (scratch_alloc(&mem, b_out + 2 * b_scr + al256((size_t)K * sizeof(int32_t)), s) != cudaSuccess)
+    return SOGRAND_ENOMEM;
   float *d_in = (float *)mem;
   uint8_t *d_bits = (uint8_t *)(mem + b_in);
   int32_t *d_hi = (int32_t *)(mem + b_in + b_bits);
   uint8_t *d_st = (uint8_t *)(mem + b_in + b_bits + al256((size_t)F * 4));
   int64_t *d_q = (int64_t *)(mem + b_in + b_bits + al256((size_t)F * 4) + al256((size_t)F));
-  int32_t *d_err = (int32_t *)(mem + b_out + 2 * b_scr);  // one timeout flag per chunk (K <= 8)
+  int32_t *d_err = (int32_t *)(mem + b_out + 2 * b_scr);  // one timeout flag per chunk
   const sg::SisoParams P = siso_params(L, cap, thr);
   cudaStream_t st[4] = {nullptr, nullptr, nullptr, nullptr};  // h2d, decode x2, d2h
   std::vector<cudaEvent_t> ev;
@@ -1017,11 +1029,11 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
     return x;
   };
   cudaEvent_t start = event();
-  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, 8 * sizeof(int32_t), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(d_err, 0, (size_t)K * sizeof(int32_t), s);
   if (e == cudaSuccess) e = cudaEventRecord(start, s);
   for (int i = 0; i < 4 && e == cudaSuccess; i++) e = cudaStreamWaitEvent(st[i], start, 0);
   for (int64_t k = 0; k < K && e == cudaSuccess; k++) {
-    const int64_t f0 = k * chunk, Fk = std::min(chunk, F - f0);
+    const int64_t f0 = starts[k], Fk = starts[k + 1] - starts[k];
     if (Fk <= 0) break;
     cudaStream_t sd = st[1 + (k & 1)];
     cudaEvent_t in_done = event(), dec_done = event();
@@ -1045,8 +1057,9 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
     if (e == cudaSuccess && queries)
       e = cudaMemcpyAsync(queries + f0, d_q + f0, Fk * 8, cudaMemcpyDeviceToHost, st[3]);
   }
-  int32_t err[8] = {0};
-  if (e == cudaSuccess) e = cudaMemcpyAsync(err, d_err, sizeof(err), cudaMemcpyDeviceToHost, st[3]);
+  std::vector<int32_t> err((size_t)K, 0);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(err.data(), d_err, (size_t)K * sizeof(int32_t), cudaMemcpyDeviceToHost, st[3]);
   // the caller's stream resumes after every stage
   for (int i = 0; i < 4 && st[i]; i++) {
     cudaEvent_t x = event();
@@ -1059,7 +1072,7 @@ int product_decode_host(sogrand_code *rc_, const sogrand_code *cc_, int64_t F, c
   for (int i = 0; i < 4; i++)
     if (st[i]) cudaStreamDestroy(st[i]);
   if (e != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) return SOGRAND_ECUDA;
-  for (int k = 0; k < 8; k++)
+  for (int64_t k = 0; k < K; k++)
     if (err[k]) return SOGRAND_ETIMEOUT;
   return SOGRAND_OK;
 }
